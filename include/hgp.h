@@ -1,0 +1,177 @@
+/*
+ * hgp.h -- C ABI of the GB300 library for incidence-constrained multilevel
+ * hypergraph partitioning ("Incidence Constraints in Hypergraph Partitioning
+ * on GPU", arXiv 2604.14411).
+ *
+ * Problem (Sec. II-A): a directed hypergraph G(N, E, omega); every hyperedge
+ * e is a set of pins whose FIRST pin is its source src(e) and whose other
+ * pins are its destinations dst(e).  in(n) = {e : n in dst(e)}.  A
+ * partition rho must satisfy, for every part p,
+ *     sum of node weights in p            <= Omega
+ *     |union of in(n) over n in p|        <= Delta
+ * and the method minimises the connectivity of Eq. (1),
+ *     Conn = sum_e omega(e) * (number of distinct parts among e's pins - 1).
+ *
+ * Method (Sec. II-B, III, IV): coarsening levels (Eq. (2) neighbour scores,
+ * bound-checked candidate per node, matching on the pairing pseudo-forest,
+ * contraction) until ceil(W / Omega) nodes remain or no pair can merge; the
+ * coarsest clusters are the initial parts; then per level, from coarsest to
+ * finest, one or more refinement passes (Eq. (3) moves, sorted sequence,
+ * in-sequence gains, best valid prefix) followed by projection.
+ *
+ * All computation runs in CUDA kernels on the current device, in stream
+ * order on the stream given to hgp_create.  Ids and CSR offsets are int32;
+ * the total pin count must be < 2^31.
+ *
+ * Thread safety: a handle is used by one host thread at a time.  Different
+ * handles are independent.
+ * Errors: every entry point returns an hgp_status; nothing is thrown across
+ * the ABI.  hgp_last_error() gives a message for the last failure on a
+ * handle.
+ */
+#ifndef HGP_H
+#define HGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HGP_OK = 0,
+    HGP_ERR_INVALID_ARG = 1,   /* bad CSR, weights or bounds (see hgp_create) */
+    HGP_ERR_INFEASIBLE = 2,    /* a single node already exceeds Omega or Delta */
+    HGP_ERR_OOM = 3,           /* device allocation failed */
+    HGP_ERR_CUDA = 4,          /* a CUDA call failed (message has the detail) */
+    HGP_ERR_DEVICE_LIMIT = 5,  /* a bounded device loop ran out of its budget */
+    HGP_ERR_STATE = 6          /* call not valid in the handle's current state */
+} hgp_status;
+
+/* hgp_create flags */
+#define HGP_INPUT_DEVICE 1u    /* offsets/pins/weights are device pointers */
+
+/* hgp_result.out_flags */
+#define HGP_OUTPUT_DEVICE 1u   /* part_ids/part_weight/part_inbound are device pointers */
+
+/* hgp_options.debug bits */
+#define HGP_DEBUG_KEEP_LEVELS 1u   /* keep per-level arrays for hgp_get_level_array */
+#define HGP_DEBUG_TIMING 2u        /* time every phase with CUDA events (hgp_get_stats) */
+#define HGP_DEBUG_FORCE_GLOBAL 4u  /* test knob: use the global-memory tables of the large-level
+                                      paths for scoring and proposals at every level */
+#define HGP_DEBUG_NO_BITMAP 8u     /* test knob: test in(n) membership by binary search instead
+                                      of the shared-memory bitmap */
+
+typedef struct hgp_graph hgp_graph;
+
+/*
+ * Build a hypergraph handle (the level-0 incidence structure of Sec. II-C:
+ * pins of every hyperedge, and per node the sorted sets I(n) = in(n) u out(n)
+ * and in(n)).
+ *   num_nodes     |N| >= 1
+ *   num_edges     |E| >= 0
+ *   offsets       [num_edges + 1] int32, offsets[0] = 0, strictly increasing
+ *                 (no empty hyperedge), offsets[E] = total pins < 2^31
+ *   pins          [offsets[E]] int32 node ids in [0, num_nodes); first pin of
+ *                 each edge is its source; no repeated pin within an edge
+ *   node_weights  [num_nodes] int32 >= 1, or NULL for unit weights;
+ *                 their sum must be < 2^31
+ *   edge_weights  [num_edges] int32 >= 1, or NULL for unit weights (omega);
+ *                 their sum must be < 2^31
+ *   flags         HGP_INPUT_DEVICE: the four arrays are device memory
+ *                 readable on `stream`; otherwise host memory
+ *   stream        cudaStream_t to run on (NULL = default stream)
+ *   out           receives the handle
+ * Ownership: inputs are copied; the caller may free them once the call has
+ * returned (device inputs: once `stream` has reached this point).
+ * Errors: HGP_ERR_INVALID_ARG for any violated rule above (checked on the
+ * device), HGP_ERR_OOM, HGP_ERR_CUDA.  On error *out is NULL.
+ */
+int hgp_create(int32_t num_nodes, int32_t num_edges,
+               const int32_t *offsets, const int32_t *pins,
+               const int32_t *node_weights, const int32_t *edge_weights,
+               uint32_t flags, void *stream, hgp_graph **out);
+
+typedef struct {
+    int32_t refine_passes;     /* refinement passes per level (default 1; 0 = none) */
+    uint32_t debug;            /* HGP_DEBUG_* bits */
+    int32_t reserved[6];       /* must be zero */
+} hgp_options;
+
+typedef struct {
+    /* caller-provided outputs */
+    int32_t *part_ids;         /* [num_nodes]: compacted part of every node (required) */
+    int64_t *part_weight;      /* [num_nodes] or NULL: node weight of part p at [p] */
+    int32_t *part_inbound;     /* [num_nodes] or NULL: |union in(n)| of part p at [p] */
+    uint32_t out_flags;        /* HGP_OUTPUT_DEVICE: the three arrays are device memory */
+    /* filled by hgp_partition */
+    int64_t cost;              /* Eq. (1) connectivity of the result */
+    int32_t num_parts;         /* parts are numbered 0..num_parts-1 */
+    int32_t num_levels;        /* coarsening levels built (including level 0) */
+} hgp_result;
+
+/*
+ * Partition the handle's hypergraph under node bound `omega` (>= 1) and
+ * inbound-hyperedge bound `delta` (>= 0).  Parts are the non-empty clusters
+ * of the final partition, renumbered 0..num_parts-1 in the order of their
+ * internal ids.  The result is a pure function of (graph, omega, delta,
+ * refine_passes).
+ * Returns HGP_ERR_INFEASIBLE when some node alone has weight > omega or
+ * |in(n)| > delta (then no partition exists), HGP_ERR_INVALID_ARG for bad
+ * bounds/options/null part_ids.  Host outputs are complete on return; device
+ * outputs are complete when `stream` reaches the end of the call.
+ */
+int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta,
+                  const hgp_options *opt, hgp_result *res);
+
+#define HGP_MAX_STAT_LEVELS 4096
+typedef struct {
+    int32_t num_levels;        /* levels of the last hgp_partition */
+    int32_t num_parts;
+    int64_t cost;
+    double ms_create;          /* hgp_create wall time (host clock) */
+    double ms_partition;       /* last hgp_partition wall time (host clock) */
+    /* HGP_DEBUG_TIMING only (CUDA-event times, summed over levels): */
+    double ms_coarsen;         /* first scoring kernel .. last contraction */
+    double ms_refine;          /* refinement and projection */
+    double ms_score;           /* scoring kernel (Eq. (2) + deferred checks) */
+    double ms_match;           /* matching + gamma */
+    double ms_contract;        /* contraction */
+    int64_t score_launches;
+    int64_t score_bytes;       /* algorithmic bytes of all scoring launches */
+    int64_t contract_bytes;    /* algorithmic bytes of all contractions */
+    int64_t pins_total;        /* sum over built levels of the pin count */
+    int64_t kernel_launches;   /* kernels launched by the last hgp_partition */
+    int64_t moves_applied;     /* refinement moves applied, all levels */
+} hgp_stats;
+
+/* Statistics of the handle's last hgp_partition (and hgp_create). */
+int hgp_get_stats(const hgp_graph *g, hgp_stats *st);
+
+/* Per-level arrays kept by HGP_DEBUG_KEEP_LEVELS (copied to host). */
+enum {
+    HGP_LEVEL_PAIR = 0,        /* [V_l] candidate of each node, -1 = none */
+    HGP_LEVEL_SCORE = 1,       /* [V_l] hist(n, pair(n)), 0 when none */
+    HGP_LEVEL_MATCH = 2,       /* [V_l] matched partner (self = single) */
+    HGP_LEVEL_GAMMA = 3,       /* [V_l] coarse node of each node */
+    HGP_LEVEL_RHO_IN = 4,      /* [V_l] partition entering refinement */
+    HGP_LEVEL_RHO_OUT = 5,     /* [V_l] partition after refinement */
+    HGP_LEVEL_WEIGHT = 6,      /* [V_l] node weights */
+    HGP_LEVEL_REFINE = 7       /* [3] proposed moves, applied prefix, gain (as int64) */
+};
+/* Length of array `which` of level l (-1 if absent). */
+int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which);
+/* Copies array `which` of level l into host buffer out (int64 elements). */
+int hgp_get_level_array(const hgp_graph *g, int32_t level, int32_t which, int64_t *out);
+
+const char *hgp_error_string(int status);
+const char *hgp_last_error(const hgp_graph *g);
+
+/* Frees the handle and all device memory it owns (after syncing its stream). */
+void hgp_destroy(hgp_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGP_H */

@@ -1,0 +1,506 @@
+// C ABI of the library (include/hgp.h): handle lifetime, the level loop of
+// Sec. II-B (coarsen until ceil(W / Omega) nodes or no merge, then refine
+// from the coarsest level down while projecting), and result delivery.
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hgp_internal.cuh"
+
+namespace hgp {
+cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
+                      int32_t *pair, int32_t *score, int32_t *status,
+                      unsigned long long *bytes, uint32_t debug, cudaStream_t s);
+cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
+                      int32_t *match, int32_t *gamma, int32_t *d_V2, int32_t *status,
+                      cudaStream_t s);
+cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
+                         int32_t *status, cudaStream_t s);
+int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
+                     cudaError_t *cerr, std::string *why, cudaStream_t s);
+struct RefineOut {
+    int32_t M, kstar;
+    long long gain;
+};
+cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
+                            int32_t K, int64_t omega, int64_t delta, RefineOut *out,
+                            uint32_t debug, cudaStream_t s);
+void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
+                 cudaStream_t s);
+cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
+                         int32_t K, int32_t *part_ids, int64_t *pw, int32_t *pin,
+                         unsigned long long *d_cost, int32_t *d_nparts, cudaStream_t s);
+
+__global__ void k_node_maxima(int32_t N, const int32_t *w, const int32_t *noff, int32_t *out) {
+    int32_t mw = 0, mi = 0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        mw = max(mw, w[n]);
+        mi = max(mi, noff[n + 1] - noff[n]);
+    }
+    atomicMax(&out[0], mw);
+    atomicMax(&out[1], mi);
+}
+
+__global__ void k_fill_one(int32_t *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 1;
+}
+}  // namespace hgp
+
+using namespace hgp;
+
+struct hgp_graph {
+    cudaStream_t stream = nullptr;
+    Arena keep;
+    Level L0;
+    int32_t *ew = nullptr;
+    int32_t N = 0, E = 0;
+    int64_t W = 0;
+    int32_t max_w = 0, max_in = 0;
+    std::string err;
+    hgp_stats stats{};
+    std::vector<std::vector<int64_t>> dbg[8];
+};
+
+static int fail(hgp_graph *g, int code, const std::string &msg) {
+    if (g) g->err = msg;
+    return code;
+}
+
+static int cuda_fail(hgp_graph *g, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();   // clear a sticky launch error state where possible
+    if (e == cudaErrorMemoryAllocation) return fail(g, HGP_ERR_OOM, m);
+    return fail(g, HGP_ERR_CUDA, m);
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return cuda_fail(g, _e, where); \
+    } while (0)
+
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+static thread_local std::string t_create_err;
+
+extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *offsets,
+                          const int32_t *pins, const int32_t *node_weights,
+                          const int32_t *edge_weights, uint32_t flags, void *stream,
+                          hgp_graph **out) {
+    if (!out) return HGP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (num_nodes < 1 || num_edges < 0 || !offsets || (num_edges > 0 && !pins))
+        return HGP_ERR_INVALID_ARG;
+    if ((flags & ~HGP_INPUT_DEVICE) != 0) return HGP_ERR_INVALID_ARG;
+    double t0 = now_ms();
+    hgp_graph *g = new (std::nothrow) hgp_graph();
+    if (!g) return HGP_ERR_OOM;
+    g->stream = (cudaStream_t)stream;
+    g->keep.stream = g->stream;
+    g->N = num_nodes;
+    g->E = num_edges;
+    cudaStream_t s = g->stream;
+    bool dev = (flags & HGP_INPUT_DEVICE) != 0;
+    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    Level &L = g->L0;
+    L.V = num_nodes;
+    L.E = num_edges;
+    auto bail = [&](int code) {
+        cudaStreamSynchronize(s);
+        g->keep.release_all();
+        cudaStreamSynchronize(s);
+        t_create_err = g->err;
+        delete g;
+        return code;
+    };
+#define CKC(expr, where)                                             \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return bail(cuda_fail(g, _e, where)); \
+    } while (0)
+    CKC(dalloc(g->keep, &L.poff, (size_t)num_edges + 1), "alloc offsets");
+    CKC(cudaMemcpyAsync(L.poff, offsets, sizeof(int32_t) * ((size_t)num_edges + 1), kind, s),
+        "copy offsets");
+    int32_t P = 0;
+    if (dev) {
+        CKC(cudaMemcpyAsync(&P, L.poff + num_edges, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+            "read pin count");
+        CKC(cudaStreamSynchronize(s), "sync");
+    } else {
+        P = offsets[num_edges];
+    }
+    if (P < 0 || (num_edges > 0 && P < num_edges)) {
+        g->err = "offsets[num_edges] must be the pin count (>= one pin per edge)";
+        return bail(HGP_ERR_INVALID_ARG);
+    }
+    CKC(dalloc(g->keep, &L.pins, P), "alloc pins");
+    if (P > 0)
+        CKC(cudaMemcpyAsync(L.pins, pins, sizeof(int32_t) * (size_t)P, kind, s), "copy pins");
+    CKC(dalloc(g->keep, &L.w, num_nodes), "alloc node weights");
+    CKC(dalloc(g->keep, &g->ew, num_edges), "alloc edge weights");
+    if (node_weights)
+        CKC(cudaMemcpyAsync(L.w, node_weights, sizeof(int32_t) * (size_t)num_nodes, kind, s),
+            "copy node weights");
+    else
+        fill_i32(L.w, 1, num_nodes, s);
+    if (num_edges > 0) {
+        if (edge_weights)
+            CKC(cudaMemcpyAsync(g->ew, edge_weights, sizeof(int32_t) * (size_t)num_edges, kind, s),
+                "copy edge weights");
+        else
+            fill_i32(g->ew, 1, num_edges, s);
+    }
+    Arena tmp;
+    tmp.stream = s;
+    cudaError_t ce = cudaSuccess;
+    std::string why;
+    int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, &ce, &why, s);
+    if (rc != 0) {
+        tmp.release_all();
+        if (rc < 0) return bail(cuda_fail(g, ce, "build level 0"));
+        g->err = why;
+        return bail(HGP_ERR_INVALID_ARG);
+    }
+    // node maxima and total weight for the singleton check and the stop rule
+    int32_t *mx = nullptr;
+    CKC(dalloc(tmp, &mx, 2), "alloc");
+    CKC(cudaMemsetAsync(mx, 0, sizeof(int32_t) * 2, s), "memset");
+    k_node_maxima<<<num_sms() * 4, 256, 0, s>>>(num_nodes, L.w, L.noff, mx);
+    count_launch();
+    int32_t hmx[2];
+    CKC(cudaMemcpyAsync(hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s), "read maxima");
+    std::vector<int32_t> hw;
+    if (node_weights) {
+        hw.resize(num_nodes);
+        CKC(cudaMemcpyAsync(hw.data(), L.w, sizeof(int32_t) * (size_t)num_nodes,
+                            cudaMemcpyDeviceToHost, s), "read weights");
+    }
+    CKC(cudaStreamSynchronize(s), "sync");
+    tmp.release_all();
+    g->max_w = hmx[0];
+    g->max_in = hmx[1];
+    int64_t W = 0;
+    if (node_weights) for (int32_t x : hw) W += x;
+    else W = num_nodes;
+    g->W = W;
+    CKC(cudaStreamSynchronize(s), "sync");
+#undef CKC
+    g->stats.ms_create = now_ms() - t0;
+    *out = g;
+    return HGP_OK;
+}
+
+namespace {
+struct Timer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];   // score, match, contract, refine
+    void start(int k, cudaEvent_t *a) {
+        if (!on) return;
+        cudaEventCreate(a);
+        cudaEventRecord(*a, s);
+        (void)k;
+    }
+    void stop(int k, cudaEvent_t a) {
+        if (!on) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, s);
+        ev[k].push_back({a, b});
+    }
+    double total(int k) {
+        double t = 0;
+        for (auto &p : ev[k]) {
+            float ms = 0;
+            cudaEventSynchronize(p.second);
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            t += ms;
+        }
+        return t;
+    }
+    ~Timer() {
+        for (auto &v : ev)
+            for (auto &p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    }
+};
+
+void keep_array(hgp_graph *g, int which, int level, const int32_t *d, int64_t n, cudaStream_t s) {
+    auto &vv = g->dbg[which];
+    if ((int)vv.size() <= level) vv.resize(level + 1);
+    std::vector<int32_t> h(n > 0 ? n : 0);
+    if (n > 0) {
+        cudaMemcpyAsync(h.data(), d, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    }
+    vv[level].assign(h.begin(), h.end());
+}
+}  // namespace
+
+extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const hgp_options *opt,
+                             hgp_result *res) {
+    if (!g || !res) return HGP_ERR_INVALID_ARG;
+    if (omega < 1 || delta < 0) return fail(g, HGP_ERR_INVALID_ARG, "omega must be >= 1 and delta >= 0");
+    if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
+    int32_t passes = 1;
+    uint32_t debug = 0;
+    if (opt) {
+        if (opt->refine_passes < 0) return fail(g, HGP_ERR_INVALID_ARG, "refine_passes must be >= 0");
+        for (int i = 0; i < 6; ++i)
+            if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
+                                     HGP_DEBUG_NO_BITMAP))
+            return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
+        passes = opt->refine_passes;
+        debug = opt->debug;
+    }
+    if (g->max_w > omega || g->max_in > delta)
+        return fail(g, HGP_ERR_INFEASIBLE, "a single node exceeds omega or delta; no partition exists");
+    double t0 = now_ms();
+    int64_t launches0 = g_launches;
+    cudaStream_t s = g->stream;
+    Arena lv, tmp;
+    lv.stream = s;
+    tmp.stream = s;
+    Timer tm;
+    tm.on = (debug & HGP_DEBUG_TIMING) != 0;
+    tm.s = s;
+    if (debug & HGP_DEBUG_KEEP_LEVELS)
+        for (auto &v : g->dbg) v.clear();
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        tmp.release_all();
+        lv.release_all();
+        cudaStreamSynchronize(s);
+    };
+#define CKP(expr, where)                                        \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) { int _r = cuda_fail(g, _e, where); cleanup(); return _r; } \
+    } while (0)
+
+    int32_t *d_status = nullptr, *d_V2 = nullptr;
+    unsigned long long *d_bytes = nullptr;
+    CKP(dalloc(lv, &d_status, 1), "alloc");
+    CKP(dalloc(lv, &d_V2, 1), "alloc");
+    CKP(dalloc(lv, &d_bytes, 1), "alloc");
+    CKP(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s), "memset");
+    CKP(cudaMemsetAsync(d_bytes, 0, sizeof(unsigned long long), s), "memset");
+
+    int64_t target = g->W / omega + (g->W % omega != 0);
+    std::vector<Level> levels;
+    levels.push_back(g->L0);
+    levels[0].gamma = nullptr;
+    levels[0].match = nullptr;
+    int32_t K = 0;
+    bool top_gamma = false;
+    int64_t pins_total = g->L0.P;
+    cudaEvent_t ev_a;
+    double c0 = now_ms();
+    if ((int64_t)g->L0.V <= target) {
+        K = g->L0.V;
+    } else {
+        for (;;) {
+            Level &L = levels.back();
+            int l = (int)levels.size() - 1;
+            int32_t *pair, *score;
+            CKP(dalloc(tmp, &pair, L.V), "alloc pair");
+            CKP(dalloc(tmp, &score, L.V), "alloc score");
+            CKP(dalloc(lv, &L.match, L.V), "alloc match");
+            CKP(dalloc(lv, &L.gamma, L.V), "alloc gamma");
+            tm.start(0, &ev_a);
+            CKP(run_score(tmp, L, g->ew, omega, delta, pair, score, d_status,
+                          tm.on ? d_bytes : nullptr, debug, s), "score");
+            tm.stop(0, ev_a);
+            tm.start(1, &ev_a);
+            CKP(run_match(tmp, L.V, pair, score, L.match, L.gamma, d_V2, d_status, s), "match");
+            tm.stop(1, ev_a);
+            int32_t h[2];
+            CKP(cudaMemcpyAsync(&h[0], d_V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read V2");
+            CKP(cudaMemcpyAsync(&h[1], d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read status");
+            CKP(cudaStreamSynchronize(s), "sync");
+            if (h[1] != 0) {
+                cleanup();
+                return fail(g, h[1] == kDevLimit ? HGP_ERR_DEVICE_LIMIT : HGP_ERR_CUDA,
+                            "device status " + std::to_string(h[1]) + " during coarsening");
+            }
+            if (debug & HGP_DEBUG_KEEP_LEVELS) {
+                keep_array(g, HGP_LEVEL_PAIR, l, pair, L.V, s);
+                keep_array(g, HGP_LEVEL_SCORE, l, score, L.V, s);
+                keep_array(g, HGP_LEVEL_MATCH, l, L.match, L.V, s);
+                keep_array(g, HGP_LEVEL_WEIGHT, l, L.w, L.V, s);
+            }
+            int32_t V2 = h[0];
+            if (V2 == L.V) {            // no cluster can be unified
+                K = L.V;
+                break;
+            }
+            if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_GAMMA, l, L.gamma, L.V, s);
+            if ((int64_t)V2 <= target) {   // coarsest clusters become the parts
+                K = V2;
+                top_gamma = true;
+                break;
+            }
+            Level H;
+            tm.start(2, &ev_a);
+            CKP(run_contract(lv, tmp, L, V2, H, d_status, s), "contract");
+            tm.stop(2, ev_a);
+            levels.push_back(H);
+            pins_total += H.P;
+            CKP(cudaStreamSynchronize(s), "sync");
+            tmp.release_all();
+        }
+    }
+    double c1 = now_ms();
+    int L = (int)levels.size() - 1;
+    if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_WEIGHT, L, levels[L].w, levels[L].V, s);
+    // initial partition of the coarsest level
+    int32_t *rho = nullptr;
+    CKP(dalloc(lv, &rho, levels[L].V), "alloc rho");
+    if (top_gamma)
+        CKP(cudaMemcpyAsync(rho, levels[L].gamma, sizeof(int32_t) * (size_t)levels[L].V,
+                            cudaMemcpyDeviceToDevice, s), "copy gamma");
+    else
+        iota_i32(rho, levels[L].V, s);
+    int64_t moves_applied = 0;
+    std::vector<int64_t> rstat;
+    tm.start(3, &ev_a);
+    for (int l = L; l >= 0; --l) {
+        const Level &Lv = levels[l];
+        if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
+        RefineOut ro{0, 0, 0};
+        for (int p = 0; p < passes; ++p) {
+            CKP(run_refine_pass(tmp, Lv, g->ew, rho, K, omega, delta, &ro, debug, s), "refine");
+            CKP(cudaStreamSynchronize(s), "sync");
+            moves_applied += ro.kstar;
+            tmp.release_all();
+        }
+        if (debug & HGP_DEBUG_KEEP_LEVELS) {
+            keep_array(g, HGP_LEVEL_RHO_OUT, l, rho, Lv.V, s);
+            auto &vv = g->dbg[HGP_LEVEL_REFINE];
+            if ((int)vv.size() <= l) vv.resize(l + 1);
+            vv[l] = {ro.M, ro.kstar, ro.gain};
+        }
+        if (l > 0) {
+            int32_t *rf = nullptr;
+            CKP(dalloc(lv, &rf, levels[l - 1].V), "alloc rho");
+            run_project(levels[l - 1].V, levels[l - 1].gamma, rho, rf, s);
+            rho = rf;
+        }
+    }
+    tm.stop(3, ev_a);
+    // result
+    bool outdev = (res->out_flags & HGP_OUTPUT_DEVICE) != 0;
+    int32_t N = g->N;
+    int32_t *d_ids = outdev ? res->part_ids : nullptr;
+    int64_t *d_pw = outdev ? res->part_weight : nullptr;
+    int32_t *d_pin = outdev ? res->part_inbound : nullptr;
+    if (!outdev) {
+        CKP(dalloc(tmp, &d_ids, N), "alloc out");
+        if (res->part_weight) CKP(dalloc(tmp, &d_pw, N), "alloc out");
+        if (res->part_inbound) CKP(dalloc(tmp, &d_pin, N), "alloc out");
+    }
+    unsigned long long *d_cost = nullptr;
+    int32_t *d_np = nullptr;
+    CKP(dalloc(tmp, &d_cost, 1), "alloc");
+    CKP(dalloc(tmp, &d_np, 1), "alloc");
+    CKP(run_finalize(tmp, g->L0, g->ew, rho, K, d_ids, d_pw, d_pin, d_cost, d_np, s), "finalize");
+    unsigned long long cost = 0;
+    int32_t np = 0;
+    CKP(cudaMemcpyAsync(&cost, d_cost, sizeof(cost), cudaMemcpyDeviceToHost, s), "read cost");
+    CKP(cudaMemcpyAsync(&np, d_np, sizeof(np), cudaMemcpyDeviceToHost, s), "read parts");
+    if (!outdev) {
+        CKP(cudaMemcpyAsync(res->part_ids, d_ids, sizeof(int32_t) * (size_t)N,
+                            cudaMemcpyDeviceToHost, s), "copy part ids");
+        CKP(cudaStreamSynchronize(s), "sync");
+        if (res->part_weight)
+            CKP(cudaMemcpyAsync(res->part_weight, d_pw, sizeof(int64_t) * (size_t)np,
+                                cudaMemcpyDeviceToHost, s), "copy part weights");
+        if (res->part_inbound)
+            CKP(cudaMemcpyAsync(res->part_inbound, d_pin, sizeof(int32_t) * (size_t)np,
+                                cudaMemcpyDeviceToHost, s), "copy part inbound");
+    }
+    CKP(cudaStreamSynchronize(s), "sync");
+    res->cost = (int64_t)cost;
+    res->num_parts = np;
+    res->num_levels = (int32_t)levels.size();
+    hgp_stats &st = g->stats;
+    double ms_create = st.ms_create;
+    std::memset(&st, 0, sizeof(st));
+    st.ms_create = ms_create;
+    st.num_levels = res->num_levels;
+    st.num_parts = np;
+    st.cost = res->cost;
+    st.pins_total = pins_total;
+    st.moves_applied = moves_applied;
+    if (tm.on) {
+        st.ms_score = tm.total(0);
+        st.ms_match = tm.total(1);
+        st.ms_contract = tm.total(2);
+        st.ms_refine = tm.total(3);
+        st.ms_coarsen = st.ms_score + st.ms_match + st.ms_contract;
+        st.score_launches = (int64_t)tm.ev[0].size();
+        unsigned long long b = 0;
+        cudaMemcpy(&b, d_bytes, sizeof(b), cudaMemcpyDeviceToHost);
+        st.score_bytes = (int64_t)b;
+    }
+    (void)c0; (void)c1;
+    st.kernel_launches = g_launches - launches0;
+    cleanup();
+    st.ms_partition = now_ms() - t0;
+    return HGP_OK;
+#undef CKP
+}
+
+extern "C" int hgp_get_stats(const hgp_graph *g, hgp_stats *st) {
+    if (!g || !st) return HGP_ERR_INVALID_ARG;
+    *st = g->stats;
+    return HGP_OK;
+}
+
+extern "C" int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which) {
+    if (!g || which < 0 || which > 7 || level < 0) return -1;
+    const auto &vv = g->dbg[which];
+    if (level >= (int)vv.size() || (vv[level].empty() && which != HGP_LEVEL_REFINE)) return -1;
+    return (int64_t)vv[level].size();
+}
+
+extern "C" int hgp_get_level_array(const hgp_graph *g, int32_t level, int32_t which, int64_t *out) {
+    int64_t n = hgp_get_level_len(g, level, which);
+    if (n < 0 || !out) return HGP_ERR_INVALID_ARG;
+    const auto &v = g->dbg[which][level];
+    for (int64_t i = 0; i < n; ++i) out[i] = v[i];
+    return HGP_OK;
+}
+
+extern "C" const char *hgp_error_string(int status) {
+    switch (status) {
+    case HGP_OK: return "ok";
+    case HGP_ERR_INVALID_ARG: return "invalid argument";
+    case HGP_ERR_INFEASIBLE: return "infeasible: a single node exceeds omega or delta";
+    case HGP_ERR_OOM: return "out of device memory";
+    case HGP_ERR_CUDA: return "CUDA error";
+    case HGP_ERR_DEVICE_LIMIT: return "device loop budget exhausted";
+    case HGP_ERR_STATE: return "invalid handle state";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *hgp_last_error(const hgp_graph *g) {
+    if (!g) return t_create_err.c_str();
+    return g->err.c_str();
+}
+
+extern "C" void hgp_destroy(hgp_graph *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    g->keep.release_all();
+    cudaStreamSynchronize(g->stream);
+    delete g;
+}

@@ -1,0 +1,119 @@
+// Internal declarations of the GB300 partitioning library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/hgp.h"
+
+namespace hgp {
+
+constexpr int kWarp = 32;
+
+// Device-side status word (first failure wins; host reads it at sync points).
+enum DevStatus : int32_t {
+    kDevOk = 0,
+    kDevLimit = 1,        // a bounded loop ran out of budget
+    kDevBadInput = 2,     // input validation failed
+    kDevInternal = 3      // a consistency check failed
+};
+
+// One level of the hierarchy, all arrays in device memory (int32 CSR).
+//   pins(e)  : poff[E+1], pins[P]  node set of each hyperedge (any order)
+//   I(n)     : ioff[V+1], inc[P]   incident hyperedges, ascending
+//   in(n)    : noff[V+1], inn[Q]   inbound hyperedges, ascending
+//   src[e]   : the level's node holding the source of e
+//   sdst[e]  : 1 when src[e] is also a destination of e at this level
+struct Level {
+    int32_t V = 0, E = 0;
+    int64_t P = 0, Q = 0;
+    int32_t *w = nullptr;
+    int32_t *poff = nullptr, *pins = nullptr;
+    int32_t *ioff = nullptr, *inc = nullptr;
+    int32_t *noff = nullptr, *inn = nullptr;
+    int32_t *src = nullptr;
+    uint8_t *sdst = nullptr;
+    int32_t *gamma = nullptr;   // [V] map to level+1 (when this level was contracted)
+    int32_t *match = nullptr;   // [V]
+};
+
+// ---------------- stream-ordered device memory ----------------
+struct Arena {
+    cudaStream_t stream = nullptr;
+    std::vector<void *> live;
+    cudaError_t alloc(void **p, size_t bytes);
+    void release_all();
+};
+
+template <typename T>
+inline cudaError_t dalloc(Arena &a, T **p, size_t count) {
+    return a.alloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+// ---------------- launch bookkeeping ----------------
+extern thread_local int64_t g_launches;
+inline void count_launch() { ++g_launches; }
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+int num_sms();
+
+// ---------------- primitives (k_prims.cu) ----------------
+// Exclusive scan of n int32 values (in may alias out); if total != null the
+// sum of all values is written to *total (device pointer).
+cudaError_t exclusive_scan_i32(Arena &a, const int32_t *in, int32_t *out, int64_t n,
+                               int32_t *total, cudaStream_t s);
+cudaError_t inclusive_scan_i64(Arena &a, const int64_t *in, int64_t *out, int64_t n,
+                               cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the
+// key.  Sorted data ends in keys_out/vals_out (may be null vals).
+cudaError_t radix_sort_pairs(Arena &a, const uint32_t *keys_in, const int32_t *vals_in,
+                             uint32_t *keys_out, int32_t *vals_out, int64_t n, int bits,
+                             cudaStream_t s);
+// Row id of every CSR entry: row_of[j] = r for off[r] <= j < off[r+1].
+void expand_rows(const int32_t *off, int32_t rows, int32_t *row_of, cudaStream_t s);
+// off[r] = exclusive prefix of counts (rows+1 entries); total in off[rows].
+cudaError_t counts_to_offsets(Arena &a, const int32_t *counts, int32_t *off, int32_t rows,
+                              cudaStream_t s);
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+
+inline int bits_for(int64_t maxval) {   // bits to hold values in [0, maxval]
+    int b = 0;
+    while (b < 32 && ((int64_t)1 << b) <= maxval) ++b;
+    return b < 1 ? 1 : b;
+}
+
+// ---------------- device helpers ----------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+// lower_bound over ascending a[lo, hi)
+__device__ __forceinline__ int32_t lower_bound_i32(const int32_t *a, int32_t lo, int32_t hi,
+                                                   int32_t x) {
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool contains_sorted(const int32_t *a, int32_t lo, int32_t hi,
+                                                int32_t x) {
+    int32_t p = lower_bound_i32(a, lo, hi, x);
+    return p < hi && a[p] == x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace hgp

@@ -1,0 +1,206 @@
+// Coarse hypergraph construction (Sec. III-B.4).
+//
+// Every coarse node c is one node or one matched pair {a, b} (a < b), so the
+// set unions of the paper are unions of at most two sorted lists:
+//   I'(c)  = I(a) u I(b)       in'(c) = in(a) u in(b)
+// A warp per coarse node merges the two sorted lists with duplicates removed:
+// each element finds its output slot from a binary search in the other list
+// and a ballot-prefix count of the duplicates before it, so the result is
+// sorted without any sort.  The lengths are counted first, prefix-summed into
+// the new offsets, then written.
+// pins'(e) = gamma(pins(e)) as a set: a pin is dropped only when it is the
+// larger member b of a pair whose smaller member a is also a pin of e (tested
+// by a binary search of e in the sorted I(a)); the rest are mapped through
+// gamma and compacted in place order with a warp ballot.  All |E| hyperedges
+// are kept.
+#include "hgp_internal.cuh"
+
+namespace hgp {
+
+__global__ void k_coarse_nodes(int32_t V, const int32_t *match, const int32_t *gamma,
+                               const int32_t *w, int32_t *rep_of, int32_t *w2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = (int32_t)i, m = match[n];
+        if (m >= n) {
+            int32_t c = gamma[n];
+            rep_of[c] = n;
+            w2[c] = w[n] + (m != n ? w[m] : 0);
+        }
+    }
+}
+
+// |A u B| (count) or the merged list (write), warp-cooperative.
+template <bool WRITE>
+__device__ int32_t warp_union(const int32_t *A, int32_t na, const int32_t *B, int32_t nb,
+                              int32_t *out) {
+    unsigned lt = (1u << lane_id()) - 1u;
+    int32_t dupA = 0;
+    for (int32_t base = 0; base < na; base += 32) {
+        int32_t i = base + lane_id();
+        bool valid = i < na;
+        int32_t x = valid ? A[i] : 0;
+        int32_t lb = valid ? lower_bound_i32(B, 0, nb, x) : 0;
+        bool inB = valid && lb < nb && B[lb] == x;
+        unsigned ball = __ballot_sync(0xffffffffu, inB);
+        if (WRITE && valid) out[i + lb - (dupA + __popc(ball & lt))] = x;
+        dupA += __popc(ball);
+    }
+    if (!WRITE) return na + nb - dupA;
+    int32_t dupB = 0;
+    for (int32_t base = 0; base < nb; base += 32) {
+        int32_t j = base + lane_id();
+        bool valid = j < nb;
+        int32_t y = valid ? B[j] : 0;
+        int32_t lb = valid ? lower_bound_i32(A, 0, na, y) : 0;
+        bool inA = valid && lb < na && A[lb] == y;
+        unsigned ball = __ballot_sync(0xffffffffu, inA);
+        if (valid && !inA) out[lb + j - (dupB + __popc(ball & lt))] = y;
+        dupB += __popc(ball);
+    }
+    return na + nb - dupA;
+}
+
+template <bool WRITE>
+__global__ void k_union(int32_t V2, const int32_t *rep_of, const int32_t *match,
+                        const int32_t *ioff, const int32_t *inc, const int32_t *noff,
+                        const int32_t *inn, int32_t *cntI, int32_t *cntN,
+                        const int32_t *ioff2, int32_t *inc2, const int32_t *noff2,
+                        int32_t *inn2) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = gw; c < V2; c += nw) {
+        int32_t a = rep_of[c], b = match[a];
+        const int32_t *Ia = inc + ioff[a], *Na = inn + noff[a];
+        int32_t nIa = ioff[a + 1] - ioff[a], nNa = noff[a + 1] - noff[a];
+        const int32_t *Ib = Ia, *Nb = Na;
+        int32_t nIb = 0, nNb = 0;
+        if (b != a) {
+            Ib = inc + ioff[b]; nIb = ioff[b + 1] - ioff[b];
+            Nb = inn + noff[b]; nNb = noff[b + 1] - noff[b];
+        }
+        int32_t ci = warp_union<WRITE>(Ia, nIa, Ib, nIb, WRITE ? inc2 + ioff2[c] : nullptr);
+        int32_t cn = warp_union<WRITE>(Na, nNa, Nb, nNb, WRITE ? inn2 + noff2[c] : nullptr);
+        if (!WRITE && lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; }
+    }
+}
+
+__device__ __forceinline__ bool keep_pin(int32_t m, int32_t e, const int32_t *match,
+                                         const int32_t *ioff, const int32_t *inc) {
+    int32_t a = match[m];
+    if (a >= m) return true;                              // m represents its pair
+    return !contains_sorted(inc, ioff[a], ioff[a + 1], e);  // drop if partner a is in e
+}
+
+template <bool WRITE>
+__global__ void k_coarse_pins(int32_t E, const int32_t *poff, const int32_t *pins,
+                              const int32_t *match, const int32_t *gamma, const int32_t *ioff,
+                              const int32_t *inc, int32_t *cnt, const int32_t *poff2,
+                              int32_t *pins2) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned lt = (1u << lane_id()) - 1u;
+    for (int64_t e = gw; e < E; e += nw) {
+        int32_t p0 = poff[e], p1 = poff[e + 1];
+        int32_t outpos = WRITE ? poff2[e] : 0;
+        int32_t kept = 0;
+        for (int32_t base = p0; base < p1; base += 32) {
+            int32_t j = base + lane_id();
+            bool k = false;
+            int32_t m = 0;
+            if (j < p1) {
+                m = pins[j];
+                k = keep_pin(m, (int32_t)e, match, ioff, inc);
+            }
+            unsigned ball = __ballot_sync(0xffffffffu, k);
+            if (WRITE && k) pins2[outpos + kept + __popc(ball & lt)] = gamma[m];
+            kept += __popc(ball);
+        }
+        if (!WRITE && lane_id() == 0) cnt[e] = kept;
+    }
+}
+
+__global__ void k_coarse_src(int32_t E, const int32_t *src, const uint8_t *sdst,
+                             const int32_t *gamma, const int32_t *noff2, const int32_t *inn2,
+                             int32_t *src2, uint8_t *sdst2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t e = (int32_t)i;
+        int32_t s = gamma[src[e]];
+        src2[e] = s;
+        sdst2[e] = (sdst[e] || contains_sorted(inn2, noff2[s], noff2[s + 1], e)) ? 1 : 0;
+    }
+}
+
+static int grid_warps(int64_t items) {
+    int b = div_up(items * 32, 256);
+    int cap = num_sms() * 16;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+static int grid1d(int64_t n) {
+    int b = div_up(n, 256);
+    int cap = num_sms() * 8;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+// Builds level `H` (V2 nodes) from level `L` and its match/gamma.  Device
+// allocations of H go to `keep`; temporaries to `tmp`.
+cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
+                         int32_t *status, cudaStream_t s) {
+    cudaError_t e;
+    H.V = V2;
+    H.E = L.E;
+    int32_t *rep_of = nullptr, *cntI = nullptr, *cntN = nullptr, *cntP = nullptr;
+    e = dalloc(tmp, &rep_of, V2);
+    if (!e) e = dalloc(tmp, &cntI, V2);
+    if (!e) e = dalloc(tmp, &cntN, V2);
+    if (!e) e = dalloc(tmp, &cntP, L.E);
+    if (!e) e = dalloc(keep, &H.w, V2);
+    if (!e) e = dalloc(keep, &H.ioff, (size_t)V2 + 1);
+    if (!e) e = dalloc(keep, &H.noff, (size_t)V2 + 1);
+    if (!e) e = dalloc(keep, &H.poff, (size_t)L.E + 1);
+    if (!e) e = dalloc(keep, &H.src, L.E);
+    if (!e) e = dalloc(keep, &H.sdst, L.E);
+    if (e) return e;
+    k_coarse_nodes<<<grid1d(L.V), 256, 0, s>>>(L.V, L.match, L.gamma, L.w, rep_of, H.w);
+    count_launch();
+    k_union<false><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
+                                                  L.inn, cntI, cntN, nullptr, nullptr, nullptr,
+                                                  nullptr);
+    count_launch();
+    k_coarse_pins<false><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
+                                                         L.ioff, L.inc, cntP, nullptr, nullptr);
+    count_launch();
+    e = counts_to_offsets(tmp, cntI, H.ioff, V2, s);
+    if (!e) e = counts_to_offsets(tmp, cntN, H.noff, V2, s);
+    if (!e) e = counts_to_offsets(tmp, cntP, H.poff, L.E, s);
+    if (e) return e;
+    int32_t tot[3];
+    e = cudaMemcpyAsync(&tot[0], H.ioff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&tot[1], H.noff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&tot[2], H.poff + L.E, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return e;
+    if (tot[0] != tot[2]) return cudaErrorInvalidValue;   // I' must be the transpose of pins'
+    H.P = tot[0];
+    H.Q = tot[1];
+    e = dalloc(keep, &H.inc, H.P);
+    if (!e) e = dalloc(keep, &H.inn, H.Q);
+    if (!e) e = dalloc(keep, &H.pins, H.P);
+    if (e) return e;
+    k_union<true><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
+                                                 L.inn, nullptr, nullptr, H.ioff, H.inc, H.noff,
+                                                 H.inn);
+    count_launch();
+    k_coarse_pins<true><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
+                                                        L.ioff, L.inc, nullptr, H.poff, H.pins);
+    count_launch();
+    k_coarse_src<<<grid1d(L.E), 256, 0, s>>>(L.E, L.src, L.sdst, L.gamma, H.noff, H.inn, H.src,
+                                             H.sdst);
+    count_launch();
+    (void)status;
+    return cudaGetLastError();
+}
+
+}  // namespace hgp

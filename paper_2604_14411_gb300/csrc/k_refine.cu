@@ -1,0 +1,680 @@
+// Constrained refinement (Sec. IV).
+//
+// pins(p, e) is kept sparse: for every hyperedge a list of (part, count,
+// count of destination pins) runs, sorted by part, in the hyperedge's own
+// CSR segment.  It is built by two stable radix sorts of the (edge, part)
+// pairs (by part, then by edge) and a warp per edge that compacts the runs.
+// pins_in(p, e) = pins(p, e) minus the source pin when the source is not
+// also a destination; inb(p) = #{e : pins_in(p, e) > 0} (Sec. IV-B.1).
+//
+// Proposals (Eq. (3)): a CTA per node accumulates, in a shared-memory table
+// over parts, pres(n, p) = sum of omega(e) over e in I(n) with pins(p,e) > 0;
+// then loss(n, p) = W_I(n) - pres(n, p) and gain = saving(n) - loss(n, p).
+// Parts sharing no hyperedge with n have gain <= 0, so only the parts in the
+// runs of n's hyperedges are candidates; parts with size(p) + w(n) > Omega
+// are excluded; the best gain wins, ties to the smaller part id; a move is
+// proposed iff its gain is > 0.
+//
+// Sequence: stable radix sort by gain (descending), node id ascending.
+// In-sequence gain of move k: a CTA walks I(n_k) and the pins of each
+// hyperedge, counts how the moves before k changed pins(ps, e), pins(pd, e)
+// and their destination-only variants, and applies the exact change of
+// Eq. (1); the same walk yields how many inbound hyperedges ps loses and pd
+// gains.  Validity of every prefix then follows from per-part events
+// (part, k, d_size, d_inbound): stable sort by part, per-part prefix sums,
+// transitions valid <-> invalid, and a prefix sum over k of the transition
+// deltas gives the number of violated parts after each move (Sec. IV-B.4).
+// The applied prefix is the valid one of largest summed gain (the longest
+// among equals), applied only if that gain is > 0.
+#include "hgp_internal.cuh"
+
+namespace hgp {
+
+constexpr int kPropThreads = 256;
+constexpr int kPropWarps = kPropThreads / 32;
+constexpr int kPartsDenseMax = 16384;
+
+static int grid1d(int64_t n) {
+    int b = div_up(n, 256);
+    int cap = num_sms() * 8;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+static int grid_warps(int64_t items) {
+    int b = div_up(items * 32, 256);
+    int cap = num_sms() * 16;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+// ---------------------------------------------------------------- runs
+__global__ void k_part_sizes(int32_t V, const int32_t *rho, const int32_t *w, int32_t *size) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&size[rho[n]], w[n]);
+}
+
+__global__ void k_pin_parts(int64_t P, const int32_t *pins, const int32_t *rho,
+                            const int32_t *row_of, uint32_t *kp, int32_t *ve) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        kp[j] = (uint32_t)rho[pins[j]];
+        ve[j] = row_of[j];
+    }
+}
+
+__global__ void k_runs(int32_t E, const int32_t *poff, const int32_t *parts_sorted,
+                       const int32_t *src, const uint8_t *sdst, const int32_t *rho,
+                       int32_t *rpart, int32_t *rcnt, int32_t *rcin, int32_t *rpos,
+                       int32_t *nrun, int32_t *inb) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned lt = (1u << lane_id()) - 1u;
+    for (int64_t e = gw; e < E; e += nw) {
+        int32_t p0 = poff[e], p1 = poff[e + 1];
+        int32_t r = 0;
+        for (int32_t base = p0; base < p1; base += 32) {
+            int32_t j = base + lane_id();
+            bool st = false;
+            int32_t p = 0;
+            if (j < p1) {
+                p = parts_sorted[j];
+                st = (j == p0) || parts_sorted[j - 1] != p;
+            }
+            unsigned ball = __ballot_sync(0xffffffffu, st);
+            if (st) {
+                int32_t q = p0 + r + __popc(ball & lt);
+                rpart[q] = p;
+                rpos[q] = j;
+            }
+            r += __popc(ball);
+        }
+        __syncwarp();
+        int32_t srcpart = rho[src[e]];
+        bool src_only_out = !sdst[e];
+        for (int32_t q = lane_id(); q < r; q += 32) {
+            int32_t end = (q + 1 < r) ? rpos[p0 + q + 1] : p1;
+            int32_t c = end - rpos[p0 + q];
+            int32_t p = rpart[p0 + q];
+            int32_t ci = c - ((p == srcpart && src_only_out) ? 1 : 0);
+            rcnt[p0 + q] = c;
+            rcin[p0 + q] = ci;
+            if (inb && ci > 0) atomicAdd(&inb[p], 1);
+        }
+        if (lane_id() == 0) nrun[e] = r;
+    }
+}
+
+struct Runs {
+    int32_t *rpart, *rcnt, *rcin, *nrun;
+};
+
+static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, int32_t K,
+                              Runs &R, int32_t *inb, cudaStream_t s) {
+    int64_t P = L.P;
+    int32_t *row_of, *ve, *ve2, *ps2, *rpos;
+    uint32_t *kp, *kp2, *ke2;
+    cudaError_t e = dalloc(tmp, &row_of, P);
+    if (!e) e = dalloc(tmp, &kp, P);
+    if (!e) e = dalloc(tmp, &ve, P);
+    if (!e) e = dalloc(tmp, &kp2, P);
+    if (!e) e = dalloc(tmp, &ve2, P);
+    if (!e) e = dalloc(tmp, &ke2, P);
+    if (!e) e = dalloc(tmp, &ps2, P);
+    if (!e) e = dalloc(tmp, &rpos, P);
+    if (!e) e = dalloc(tmp, &R.rpart, P);
+    if (!e) e = dalloc(tmp, &R.rcnt, P);
+    if (!e) e = dalloc(tmp, &R.rcin, P);
+    if (!e) e = dalloc(tmp, &R.nrun, L.E);
+    if (e) return e;
+    expand_rows(L.poff, L.E, row_of, s);
+    if (P > 0) {
+        k_pin_parts<<<grid1d(P), 256, 0, s>>>(P, L.pins, rho, row_of, kp, ve);
+        count_launch();
+    }
+    // stable by part, then stable by edge: each edge's segment sorted by part
+    e = radix_sort_pairs(tmp, kp, ve, kp2, ve2, P, bits_for(K > 0 ? K - 1 : 0), s);
+    if (!e) e = radix_sort_pairs(tmp, reinterpret_cast<uint32_t *>(ve2),
+                                 reinterpret_cast<int32_t *>(kp2), ke2, ps2, P,
+                                 bits_for(L.E > 0 ? L.E - 1 : 0), s);
+    if (e) return e;
+    if (L.E > 0) {
+        k_runs<<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, ps2, L.src, L.sdst, rho, R.rpart,
+                                               R.rcnt, R.rcin, rpos, R.nrun, inb);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- proposals
+struct PropArgs {
+    int32_t V, K;
+    const int32_t *w, *ioff, *inc, *poff, *ew, *rho, *size;
+    const int32_t *rpart, *rcnt, *nrun;
+    int64_t omega;
+    int32_t *gain, *pd;
+    int32_t *gpres;     // per-CTA global tables when K is large
+};
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
+    extern __shared__ __align__(16) int32_t pres_s[];
+    __shared__ unsigned long long red64[kPropWarps];
+    __shared__ long long red_s[kPropWarps], red_w[kPropWarps];
+    int32_t *pres = DENSE ? pres_s : a.gpres + (int64_t)blockIdx.x * a.K;
+    for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
+    __syncthreads();
+    for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
+        int32_t ps = a.rho[n];
+        int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
+        long long sav = 0, wI = 0;
+        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
+            int32_t e = a.inc[k];
+            int32_t we = a.ew[e];
+            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
+            if (lane_id() == 0) wI += we;
+            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
+                int32_t p = a.rpart[q];
+                if (p == ps) { if (a.rcnt[q] == 1) sav += we; }
+                else atomicAdd(&pres[p], we);
+            }
+        }
+        sav = warp_sum(sav);
+        wI = warp_sum(wI);
+        if (lane_id() == 0) { red_s[warp_id()] = sav; red_w[warp_id()] = wI; }
+        __syncthreads();
+        // best admissible part: max pres, ties to the smaller id
+        unsigned long long best = 0;
+        int32_t wn = a.w[n];
+        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
+            int32_t e = a.inc[k];
+            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
+            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
+                int32_t p = a.rpart[q];
+                if (p != ps && (int64_t)a.size[p] + wn <= a.omega) {
+                    unsigned long long key = ((unsigned long long)(uint32_t)pres[p] << 32) |
+                                             (uint32_t)(0x7fffffff - p);
+                    best = key > best ? key : best;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+            best = y > best ? y : best;
+        }
+        if (lane_id() == 0) red64[warp_id()] = best;
+        __syncthreads();
+        // clear the touched entries
+        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
+            int32_t e = a.inc[k];
+            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
+            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
+                int32_t p = a.rpart[q];
+                if (p != ps) pres[p] = 0;
+            }
+        }
+        if (threadIdx.x == 0) {
+            unsigned long long b = 0;
+            long long S = 0, W = 0;
+            for (int q = 0; q < kPropWarps; ++q) {
+                b = red64[q] > b ? red64[q] : b;
+                S += red_s[q];
+                W += red_w[q];
+            }
+            int32_t g = 0, pd = -1;
+            if (b != 0) {
+                long long presb = (long long)(b >> 32);
+                long long gain = S - (W - presb);
+                if (gain > 0) { g = (int32_t)gain; pd = 0x7fffffff - (int32_t)(b & 0xffffffffu); }
+            }
+            a.gain[n] = g;
+            a.pd[n] = pd;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- sequence
+__global__ void k_move_keys(int32_t V, const int32_t *gain, const int32_t *rank, uint32_t *key,
+                            int32_t *node) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = gain[n];
+        if (g > 0) {
+            int32_t r = rank[n];
+            key[r] = (uint32_t)(0x7fffffff - g);     // ascending key = descending gain
+            node[r] = (int32_t)n;
+        }
+    }
+}
+
+__global__ void k_move_info(int32_t M, const int32_t *mv_n, const int32_t *rho, const int32_t *pd,
+                            int32_t *mv_ps, int32_t *mv_pd, int32_t *idx_of) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = mv_n[k];
+        mv_ps[k] = rho[n];
+        mv_pd[k] = pd[n];
+        idx_of[n] = (int32_t)k;
+    }
+}
+
+__device__ __forceinline__ void run_lookup(const int32_t *rpart, const int32_t *rcnt,
+                                           const int32_t *rcin, int32_t r0, int32_t r1, int32_t p,
+                                           int32_t &c, int32_t &ci) {
+    int32_t q = lower_bound_i32(rpart, r0, r1, p);
+    if (q < r1 && rpart[q] == p) { c = rcnt[q]; ci = rcin[q]; }
+    else { c = 0; ci = 0; }
+}
+
+struct SeqArgs {
+    int32_t M;
+    const int32_t *mv_n, *mv_ps, *mv_pd, *idx_of;
+    const int32_t *ioff, *inc, *poff, *pins, *ew, *src;
+    const uint8_t *sdst;
+    const int32_t *rpart, *rcnt, *rcin, *nrun;
+    int32_t *gseq, *lose_in, *gain_in;
+};
+
+__global__ void __launch_bounds__(kPropThreads) k_seq_gain(SeqArgs a) {
+    __shared__ long long red[3][kPropWarps];
+    for (int32_t k = blockIdx.x; k < a.M; k += gridDim.x) {
+        int32_t n = a.mv_n[k], ps = a.mv_ps[k], pd = a.mv_pd[k];
+        long long g = 0, lose = 0, gainin = 0;
+        for (int32_t t = a.ioff[n] + warp_id(); t < a.ioff[n + 1]; t += kPropWarps) {
+            int32_t e = a.inc[t];
+            int32_t p0 = a.poff[e], p1 = a.poff[e + 1];
+            int32_t se = a.src[e];
+            bool sd = a.sdst[e] != 0;
+            int32_t dcs = 0, dcd = 0, dcsi = 0, dcdi = 0;
+            for (int32_t j = p0 + lane_id(); j < p1; j += 32) {
+                int32_t m = a.pins[j];
+                if (m == n) continue;
+                int32_t km = a.idx_of[m];
+                if (km < 0 || km >= k) continue;
+                int32_t pm_s = a.mv_ps[km], pm_d = a.mv_pd[km];
+                int32_t ds = (pm_d == ps) - (pm_s == ps);
+                int32_t dd = (pm_d == pd) - (pm_s == pd);
+                dcs += ds;
+                dcd += dd;
+                if (m != se || sd) { dcsi += ds; dcdi += dd; }
+            }
+            dcs = warp_sum(dcs);
+            dcd = warp_sum(dcd);
+            dcsi = warp_sum(dcsi);
+            dcdi = warp_sum(dcdi);
+            if (lane_id() == 0) {
+                int32_t r0 = p0, r1 = p0 + a.nrun[e];
+                int32_t cs, csi, cd, cdi;
+                run_lookup(a.rpart, a.rcnt, a.rcin, r0, r1, ps, cs, csi);
+                run_lookup(a.rpart, a.rcnt, a.rcin, r0, r1, pd, cd, cdi);
+                cs += dcs; cd += dcd; csi += dcsi; cdi += dcdi;
+                int32_t we = a.ew[e];
+                g += (long long)we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
+                if (n != se || sd) {        // e is inbound to n
+                    lose += (csi == 1) ? 1 : 0;
+                    gainin += (cdi == 0) ? 1 : 0;
+                }
+            }
+        }
+        if (lane_id() == 0) { red[0][warp_id()] = g; red[1][warp_id()] = lose; red[2][warp_id()] = gainin; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long G = 0, Lo = 0, Gi = 0;
+            for (int q = 0; q < kPropWarps; ++q) { G += red[0][q]; Lo += red[1][q]; Gi += red[2][q]; }
+            a.gseq[k] = (int32_t)G;
+            a.lose_in[k] = (int32_t)Lo;
+            a.gain_in[k] = (int32_t)Gi;
+        }
+        __syncthreads();
+    }
+}
+
+// events: 2 per move, (ps, k, -w, -lose) then (pd, k, +w, +gain_in)
+__global__ void k_events(int32_t M, const int32_t *mv_n, const int32_t *mv_ps, const int32_t *mv_pd,
+                         const int32_t *w, uint32_t *ekey, int32_t *eid) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        ekey[2 * k] = (uint32_t)mv_ps[k];
+        ekey[2 * k + 1] = (uint32_t)mv_pd[k];
+        eid[2 * k] = (int32_t)(2 * k);
+        eid[2 * k + 1] = (int32_t)(2 * k + 1);
+    }
+}
+
+__global__ void k_event_deltas(int64_t nev, const int32_t *eid_sorted, const int32_t *mv_n,
+                               const int32_t *w, const int32_t *lose_in, const int32_t *gain_in,
+                               int64_t *dsz, int64_t *dinb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t id = eid_sorted[i];
+        int32_t k = id >> 1;
+        bool leave = (id & 1) == 0;
+        int32_t wn = w[mv_n[k]];
+        dsz[i] = leave ? -wn : wn;
+        dinb[i] = leave ? -lose_in[k] : gain_in[k];
+    }
+}
+
+__global__ void k_transitions(int64_t nev, const uint32_t *ekey_sorted, const int32_t *eid_sorted,
+                              const int64_t *csz, const int64_t *cinb, const int32_t *size0,
+                              const int32_t *inb0, int64_t omega, int64_t delta, int32_t *vdelta) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t p = ekey_sorted[i];
+        // first event of this part
+        int64_t lo = 0, hi = i;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (ekey_sorted[mid] < p) lo = mid + 1; else hi = mid;
+        }
+        int64_t start = lo;
+        int64_t bsz = start > 0 ? csz[start - 1] : 0;
+        int64_t binb = start > 0 ? cinb[start - 1] : 0;
+        int64_t s_after = size0[p] + (csz[i] - bsz);
+        int64_t n_after = inb0[p] + (cinb[i] - binb);
+        bool v_after = s_after <= omega && n_after <= delta;
+        bool v_before;
+        if (i == start) {
+            v_before = (int64_t)size0[p] <= omega && (int64_t)inb0[p] <= delta;
+        } else {
+            int64_t sb = size0[p] + (csz[i - 1] - bsz);
+            int64_t nb = inb0[p] + (cinb[i - 1] - binb);
+            v_before = sb <= omega && nb <= delta;
+        }
+        int32_t k = eid_sorted[i] >> 1;
+        if (v_before && !v_after) atomicAdd(&vdelta[k], 1);
+        if (!v_before && v_after) atomicAdd(&vdelta[k], -1);
+    }
+}
+
+__global__ void k_gseq_i64(int32_t M, const int32_t *gseq, const int32_t *vdelta, int64_t *g64,
+                           int64_t *v64) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        g64[k] = gseq[k];
+        v64[k] = vdelta[k];
+    }
+}
+
+// single CTA: k* = argmax over valid prefixes of (G, length); apply iff G > 0
+__global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32_t *kstar,
+                         long long *gain) {
+    __shared__ long long bg[1024];
+    __shared__ int32_t bk[1024];
+    long long g = 0;
+    int32_t kk = 0;
+    for (int32_t k = threadIdx.x; k < M; k += blockDim.x) {
+        if (viol[k] != 0) continue;
+        long long gk = G[k];
+        if (kk == 0 || gk > g || (gk == g && k + 1 > kk)) { g = gk; kk = k + 1; }
+    }
+    bg[threadIdx.x] = g;
+    bk[threadIdx.x] = kk;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            long long g2 = bg[threadIdx.x + o];
+            int32_t k2 = bk[threadIdx.x + o];
+            if (k2 != 0 && (bk[threadIdx.x] == 0 || g2 > bg[threadIdx.x] ||
+                            (g2 == bg[threadIdx.x] && k2 > bk[threadIdx.x]))) {
+                bg[threadIdx.x] = g2;
+                bk[threadIdx.x] = k2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bool apply = bk[0] != 0 && bg[0] > 0;
+        *kstar = apply ? bk[0] : 0;
+        *gain = apply ? bg[0] : 0;
+    }
+}
+
+__global__ void k_apply(int32_t M, const int32_t *kstar, const int32_t *mv_n, const int32_t *mv_pd,
+                        int32_t *rho) {
+    int32_t ks = *kstar;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ks && k < M;
+         k += (int64_t)gridDim.x * blockDim.x)
+        rho[mv_n[k]] = mv_pd[k];
+}
+
+__global__ void k_project(int32_t V, const int32_t *gamma, const int32_t *rho_coarse,
+                          int32_t *rho_fine) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        rho_fine[n] = rho_coarse[gamma[n]];
+}
+
+void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
+                 cudaStream_t s) {
+    if (V <= 0) return;
+    k_project<<<grid1d(V), 256, 0, s>>>(V, gamma, rho_c, rho_f);
+    count_launch();
+}
+
+__global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        flag[n] = gain[n] > 0 ? 1 : 0;
+}
+
+struct RefineOut {
+    int32_t M, kstar;
+    long long gain;
+};
+
+// One refinement pass on level L; rho is updated in place on the device.
+cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
+                            int32_t K, int64_t omega, int64_t delta, RefineOut *out,
+                            uint32_t debug, cudaStream_t s) {
+    out->M = 0; out->kstar = 0; out->gain = 0;
+    int32_t V = L.V;
+    int32_t *size, *inb;
+    cudaError_t e = dalloc(tmp, &size, K);
+    if (!e) e = dalloc(tmp, &inb, K);
+    if (e) return e;
+    cudaMemsetAsync(size, 0, sizeof(int32_t) * (size_t)K, s);
+    cudaMemsetAsync(inb, 0, sizeof(int32_t) * (size_t)K, s);
+    k_part_sizes<<<grid1d(V), 256, 0, s>>>(V, rho, L.w, size);
+    count_launch();
+    Runs R{};
+    e = build_runs(tmp, L, rho, K, R, inb, s);
+    if (e) return e;
+    // proposals
+    int32_t *pg, *ppd;
+    e = dalloc(tmp, &pg, V);
+    if (!e) e = dalloc(tmp, &ppd, V);
+    if (e) return e;
+    PropArgs pa{};
+    pa.V = V; pa.K = K; pa.w = L.w; pa.ioff = L.ioff; pa.inc = L.inc; pa.poff = L.poff;
+    pa.ew = ew; pa.rho = rho; pa.size = size; pa.rpart = R.rpart; pa.rcnt = R.rcnt;
+    pa.nrun = R.nrun; pa.omega = omega; pa.gain = pg; pa.pd = ppd;
+    int sms = num_sms();
+    if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
+        size_t smem = sizeof(int32_t) * (size_t)K;
+        e = cudaFuncSetAttribute(k_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true>, kPropThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+        int blocks = sms * per_sm;
+        if (blocks > V) blocks = V;
+        k_propose<true><<<blocks, kPropThreads, smem, s>>>(pa);
+    } else {
+        int blocks = sms * 4;
+        if (blocks > V) blocks = V;
+        e = dalloc(tmp, &pa.gpres, (size_t)blocks * K);
+        if (e) return e;
+        k_propose<false><<<blocks, kPropThreads, 0, s>>>(pa);
+    }
+    count_launch();
+    // compact proposals in node order, read M
+    int32_t *flag, *rank, *dM;
+    e = dalloc(tmp, &flag, V);
+    if (!e) e = dalloc(tmp, &rank, V);
+    if (!e) e = dalloc(tmp, &dM, 1);
+    if (e) return e;
+    k_gain_flag<<<grid1d(V), 256, 0, s>>>(V, pg, flag);
+    count_launch();
+    e = exclusive_scan_i32(tmp, flag, rank, V, dM, s);
+    if (e) return e;
+    int32_t M = 0;
+    e = cudaMemcpyAsync(&M, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return e;
+    out->M = M;
+    if (M == 0) return cudaSuccess;
+    uint32_t *mkey, *mkey2;
+    int32_t *mnode, *mv_n, *mv_ps, *mv_pd, *idx_of, *gseq, *lose, *gin;
+    e = dalloc(tmp, &mkey, M);
+    if (!e) e = dalloc(tmp, &mkey2, M);
+    if (!e) e = dalloc(tmp, &mnode, M);
+    if (!e) e = dalloc(tmp, &mv_n, M);
+    if (!e) e = dalloc(tmp, &mv_ps, M);
+    if (!e) e = dalloc(tmp, &mv_pd, M);
+    if (!e) e = dalloc(tmp, &idx_of, V);
+    if (!e) e = dalloc(tmp, &gseq, M);
+    if (!e) e = dalloc(tmp, &lose, M);
+    if (!e) e = dalloc(tmp, &gin, M);
+    if (e) return e;
+    k_move_keys<<<grid1d(V), 256, 0, s>>>(V, pg, rank, mkey, mnode);
+    count_launch();
+    e = radix_sort_pairs(tmp, mkey, mnode, mkey2, mv_n, M, 31, s);
+    if (e) return e;
+    fill_i32(idx_of, -1, V, s);
+    k_move_info<<<grid1d(M), 256, 0, s>>>(M, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
+    count_launch();
+    SeqArgs sa{};
+    sa.M = M; sa.mv_n = mv_n; sa.mv_ps = mv_ps; sa.mv_pd = mv_pd; sa.idx_of = idx_of;
+    sa.ioff = L.ioff; sa.inc = L.inc; sa.poff = L.poff; sa.pins = L.pins; sa.ew = ew;
+    sa.src = L.src; sa.sdst = L.sdst; sa.rpart = R.rpart; sa.rcnt = R.rcnt; sa.rcin = R.rcin;
+    sa.nrun = R.nrun; sa.gseq = gseq; sa.lose_in = lose; sa.gain_in = gin;
+    {
+        int blocks = sms * 8;
+        if (blocks > M) blocks = M;
+        k_seq_gain<<<blocks, kPropThreads, 0, s>>>(sa);
+        count_launch();
+    }
+    // prefix validity from per-part events
+    int64_t nev = 2 * (int64_t)M;
+    uint32_t *ekey, *ekey2;
+    int32_t *eid, *eid2, *vdelta;
+    int64_t *dsz, *dinb, *csz, *cinb, *g64, *v64, *G, *viol;
+    e = dalloc(tmp, &ekey, nev);
+    if (!e) e = dalloc(tmp, &ekey2, nev);
+    if (!e) e = dalloc(tmp, &eid, nev);
+    if (!e) e = dalloc(tmp, &eid2, nev);
+    if (!e) e = dalloc(tmp, &dsz, nev);
+    if (!e) e = dalloc(tmp, &dinb, nev);
+    if (!e) e = dalloc(tmp, &csz, nev);
+    if (!e) e = dalloc(tmp, &cinb, nev);
+    if (!e) e = dalloc(tmp, &vdelta, M);
+    if (!e) e = dalloc(tmp, &g64, M);
+    if (!e) e = dalloc(tmp, &v64, M);
+    if (!e) e = dalloc(tmp, &G, M);
+    if (!e) e = dalloc(tmp, &viol, M);
+    if (e) return e;
+    k_events<<<grid1d(M), 256, 0, s>>>(M, mv_n, mv_ps, mv_pd, L.w, ekey, eid);
+    count_launch();
+    e = radix_sort_pairs(tmp, ekey, eid, ekey2, eid2, nev, bits_for(K > 0 ? K - 1 : 0), s);
+    if (e) return e;
+    k_event_deltas<<<grid1d(nev), 256, 0, s>>>(nev, eid2, mv_n, L.w, lose, gin, dsz, dinb);
+    count_launch();
+    e = inclusive_scan_i64(tmp, dsz, csz, nev, s);
+    if (!e) e = inclusive_scan_i64(tmp, dinb, cinb, nev, s);
+    if (e) return e;
+    cudaMemsetAsync(vdelta, 0, sizeof(int32_t) * (size_t)M, s);
+    k_transitions<<<grid1d(nev), 256, 0, s>>>(nev, ekey2, eid2, csz, cinb, size, inb, omega, delta,
+                                              vdelta);
+    count_launch();
+    k_gseq_i64<<<grid1d(M), 256, 0, s>>>(M, gseq, vdelta, g64, v64);
+    count_launch();
+    e = inclusive_scan_i64(tmp, g64, G, M, s);
+    if (!e) e = inclusive_scan_i64(tmp, v64, viol, M, s);
+    if (e) return e;
+    int32_t *dk;
+    long long *dg;
+    e = dalloc(tmp, &dk, 1);
+    if (!e) e = dalloc(tmp, &dg, 1);
+    if (e) return e;
+    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, dg);
+    count_launch();
+    k_apply<<<grid1d(M), 256, 0, s>>>(M, dk, mv_n, mv_pd, rho);
+    count_launch();
+    e = cudaMemcpyAsync(&out->kstar, dk, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&out->gain, dg, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e) return e;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- output
+__global__ void k_nonempty(int32_t K, const int32_t *size, int32_t *flag) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < K;
+         p += (int64_t)gridDim.x * blockDim.x)
+        flag[p] = size[p] > 0 ? 1 : 0;
+}
+
+__global__ void k_relabel(int32_t V, const int32_t *rho, const int32_t *newid, int32_t *part_ids) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        part_ids[n] = newid[rho[n]];
+}
+
+__global__ void k_part_out(int32_t K, const int32_t *size, const int32_t *inb, const int32_t *newid,
+                           int64_t *pw, int32_t *pin) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < K;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (size[p] > 0) {
+            int32_t q = newid[p];
+            if (pw) pw[q] = size[p];
+            if (pin) pin[q] = inb[p];
+        }
+    }
+}
+
+// Eq. (1): cost = sum_e omega(e) * (number of runs of e - 1)
+__global__ void k_cost(int32_t E, const int32_t *nrun, const int32_t *ew, unsigned long long *cost) {
+    unsigned long long c = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x)
+        c += (unsigned long long)ew[e] * (unsigned long long)(nrun[e] - 1);
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(cost, c);
+}
+
+// Final output on level 0 for partition rho (part ids < K): compacted ids,
+// per-part weight and distinct inbound count, connectivity and part count.
+cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
+                         int32_t K, int32_t *part_ids, int64_t *pw, int32_t *pin,
+                         unsigned long long *d_cost, int32_t *d_nparts, cudaStream_t s) {
+    int32_t *size, *inb, *flag, *newid;
+    cudaError_t e = dalloc(tmp, &size, K);
+    if (!e) e = dalloc(tmp, &inb, K);
+    if (!e) e = dalloc(tmp, &flag, K);
+    if (!e) e = dalloc(tmp, &newid, K);
+    if (e) return e;
+    cudaMemsetAsync(size, 0, sizeof(int32_t) * (size_t)K, s);
+    cudaMemsetAsync(inb, 0, sizeof(int32_t) * (size_t)K, s);
+    cudaMemsetAsync(d_cost, 0, sizeof(unsigned long long), s);
+    k_part_sizes<<<grid1d(L.V), 256, 0, s>>>(L.V, rho, L.w, size);
+    count_launch();
+    Runs R{};
+    e = build_runs(tmp, L, rho, K, R, inb, s);
+    if (e) return e;
+    k_nonempty<<<grid1d(K), 256, 0, s>>>(K, size, flag);
+    count_launch();
+    e = exclusive_scan_i32(tmp, flag, newid, K, d_nparts, s);
+    if (e) return e;
+    k_relabel<<<grid1d(L.V), 256, 0, s>>>(L.V, rho, newid, part_ids);
+    count_launch();
+    k_part_out<<<grid1d(K), 256, 0, s>>>(K, size, inb, newid, pw, pin);
+    count_launch();
+    if (L.E > 0) {
+        k_cost<<<grid1d(L.E), 256, 0, s>>>(L.E, R.nrun, ew, d_cost);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hgp

@@ -1,0 +1,252 @@
+"""ctypes binding of libhgp.so (include/hgp.h): argument marshalling only.
+
+Every step of the partitioning runs in the library's CUDA kernels.  If the
+library has not been built this module raises on import of the binding's
+functions -- there is no fallback of any kind.
+
+Host arrays are numpy int32/int64; device arrays are torch CUDA tensors
+(passed with HGP_INPUT_DEVICE / HGP_OUTPUT_DEVICE).  PyTorch is used only for
+device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhgp.so")
+
+HGP_OK, HGP_ERR_INVALID_ARG, HGP_ERR_INFEASIBLE, HGP_ERR_OOM = 0, 1, 2, 3
+HGP_ERR_CUDA, HGP_ERR_DEVICE_LIMIT, HGP_ERR_STATE = 4, 5, 6
+HGP_INPUT_DEVICE = 1
+HGP_OUTPUT_DEVICE = 1
+HGP_DEBUG_KEEP_LEVELS = 1
+HGP_DEBUG_TIMING = 2
+HGP_DEBUG_FORCE_GLOBAL = 4
+HGP_DEBUG_NO_BITMAP = 8
+(HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
+ HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE) = range(8)
+
+
+class HgpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hgp error {code}: {msg}")
+        self.code = code
+
+
+class hgp_options(ctypes.Structure):
+    _fields_ = [("refine_passes", ctypes.c_int32), ("debug", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class hgp_result(ctypes.Structure):
+    _fields_ = [("part_ids", ctypes.c_void_p), ("part_weight", ctypes.c_void_p),
+                ("part_inbound", ctypes.c_void_p), ("out_flags", ctypes.c_uint32),
+                ("cost", ctypes.c_int64), ("num_parts", ctypes.c_int32),
+                ("num_levels", ctypes.c_int32)]
+
+
+class hgp_stats(ctypes.Structure):
+    _fields_ = [("num_levels", ctypes.c_int32), ("num_parts", ctypes.c_int32),
+                ("cost", ctypes.c_int64), ("ms_create", ctypes.c_double),
+                ("ms_partition", ctypes.c_double), ("ms_coarsen", ctypes.c_double),
+                ("ms_refine", ctypes.c_double), ("ms_score", ctypes.c_double),
+                ("ms_match", ctypes.c_double), ("ms_contract", ctypes.c_double),
+                ("score_launches", ctypes.c_int64), ("score_bytes", ctypes.c_int64),
+                ("contract_bytes", ctypes.c_int64), ("pins_total", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("moves_applied", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol declared in include/hgp.h
+EXPORTS = ("hgp_create", "hgp_partition", "hgp_get_stats", "hgp_get_level_len",
+           "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libhgp.so; raises if it is missing (build it with
+    paper_2604_14411_gb300._build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhgp.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.hgp_create.argtypes = [i32, i32, vp, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.hgp_create.restype = ctypes.c_int
+    lib.hgp_partition.argtypes = [vp, i64, i64, ctypes.POINTER(hgp_options), ctypes.POINTER(hgp_result)]
+    lib.hgp_partition.restype = ctypes.c_int
+    lib.hgp_get_stats.argtypes = [vp, ctypes.POINTER(hgp_stats)]
+    lib.hgp_get_level_len.argtypes = [vp, i32, i32]
+    lib.hgp_get_level_len.restype = i64
+    lib.hgp_get_level_array.argtypes = [vp, i32, i32, vp]
+    lib.hgp_error_string.argtypes = [ctypes.c_int]
+    lib.hgp_error_string.restype = ctypes.c_char_p
+    lib.hgp_last_error.argtypes = [vp]
+    lib.hgp_last_error.restype = ctypes.c_char_p
+    lib.hgp_destroy.argtypes = [vp]
+    lib.hgp_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a) -> bool:
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(rc, handle=None):
+    if rc != HGP_OK:
+        lib = load()
+        msg = lib.hgp_last_error(handle).decode() or lib.hgp_error_string(rc).decode()
+        raise HgpError(rc, msg)
+
+
+def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None):
+    """hgp_create: returns an opaque handle.  Arrays are all host numpy int32 or
+    all torch int32 CUDA tensors."""
+    lib = load()
+    dev = _is_device(offsets)
+    arrs = [offsets, pins, node_weights, edge_weights]
+    if not dev:
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.int32) for a in arrs]
+    else:
+        for a in arrs:
+            if a is not None and (not _is_device(a) or str(a.dtype) != "torch.int32" or not a.is_contiguous()):
+                raise TypeError("device inputs must be contiguous torch.int32 CUDA tensors")
+    h = ctypes.c_void_p()
+    E = int(arrs[0].shape[0]) - 1
+    rc = lib.hgp_create(int(num_nodes), E, *[_ptr(a) for a in arrs],
+                        HGP_INPUT_DEVICE if dev else 0, _stream_handle(stream), ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def hgp_partition(handle, omega, delta, part_ids, part_weight=None, part_inbound=None,
+                  refine_passes=1, debug=0):
+    """hgp_partition into caller buffers (host numpy or device torch tensors).
+    Returns (cost, num_parts, num_levels)."""
+    lib = load()
+    opt = hgp_options(refine_passes, debug)
+    res = hgp_result()
+    res.part_ids = _ptr(part_ids)
+    res.part_weight = _ptr(part_weight)
+    res.part_inbound = _ptr(part_inbound)
+    res.out_flags = HGP_OUTPUT_DEVICE if _is_device(part_ids) else 0
+    rc = lib.hgp_partition(handle, int(omega), int(delta), ctypes.byref(opt), ctypes.byref(res))
+    _check(rc, handle)
+    return int(res.cost), int(res.num_parts), int(res.num_levels)
+
+
+def hgp_get_stats(handle) -> dict:
+    st = hgp_stats()
+    _check(load().hgp_get_stats(handle, ctypes.byref(st)), handle)
+    return st.as_dict()
+
+
+def hgp_get_level_array(handle, level, which):
+    lib = load()
+    n = lib.hgp_get_level_len(handle, int(level), int(which))
+    if n < 0:
+        return None
+    out = np.empty(max(n, 1), dtype=np.int64)
+    _check(lib.hgp_get_level_array(handle, int(level), int(which), out.ctypes.data), handle)
+    return out[:n]
+
+
+def hgp_error_string(code) -> str:
+    return load().hgp_error_string(int(code)).decode()
+
+
+def hgp_last_error(handle) -> str:
+    return load().hgp_last_error(handle).decode()
+
+
+def hgp_destroy(handle):
+    if handle:
+        load().hgp_destroy(handle)
+
+
+@dataclass
+class Result:
+    part_ids: np.ndarray
+    cost: int
+    num_parts: int
+    num_levels: int
+    part_weight: np.ndarray
+    part_inbound: np.ndarray
+
+
+class Graph:
+    """Owning wrapper around an hgp_graph handle."""
+
+    def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None):
+        self.num_nodes = int(num_nodes)
+        self._h = hgp_create(num_nodes, offsets, pins, node_weights, edge_weights, stream)
+
+    @classmethod
+    def from_hypergraph(cls, g, stream=None):
+        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream)
+
+    def partition(self, omega, delta, refine_passes=1, debug=0) -> Result:
+        ids = np.empty(self.num_nodes, dtype=np.int32)
+        pw = np.empty(self.num_nodes, dtype=np.int64)
+        pin = np.empty(self.num_nodes, dtype=np.int32)
+        cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug)
+        return Result(ids, cost, npart, nlev, pw[:npart], pin[:npart])
+
+    def partition_device(self, omega, delta, part_ids, part_weight=None, part_inbound=None,
+                         refine_passes=1, debug=0):
+        return hgp_partition(self._h, omega, delta, part_ids, part_weight, part_inbound,
+                             refine_passes, debug)
+
+    def stats(self) -> dict:
+        return hgp_get_stats(self._h)
+
+    def level_array(self, level, which):
+        return hgp_get_level_array(self._h, level, which)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            hgp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

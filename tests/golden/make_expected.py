@@ -1,0 +1,57 @@
+"""Writes stored expected results for workloads too slow for the oracle to
+run inside the test suite.  Calls only the CPU oracle and the seeded input
+generators; nothing here touches the CUDA library.
+
+    python tests/golden/make_expected.py snn16k     # 16,384-node SNN, Omega 2^10, Delta 2^12
+
+Output: tests/golden/expected_<name>.txt with the Eq. (1) cost, the number of
+parts, the number of levels, the per-level node counts, and a SHA-256 of
+the part ids (int32 little-endian) and of the per-part (weight, inbound)
+pairs.
+"""
+import hashlib
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "snn16k": (lambda: synth.snn_16k(0), 1024, 4096),
+    "snn4k": (lambda: synth.random_snn(4096, 64, 0), 256, 1024),
+}
+
+
+def digest(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def main(name: str):
+    make, omega, delta = WORKLOADS[name]
+    g = make()
+    t = time.time()
+    with oracle.Run.from_graph(g) as r:
+        res = r.partition(omega, delta)
+        levels = [r.level_V(l) for l in range(r.num_levels)]
+    secs = time.time() - t
+    stats = np.stack([res.part_weight.astype(np.int64), res.part_inbound.astype(np.int64)], axis=1)
+    path = os.path.join(ROOT, "tests", "golden", f"expected_{name}.txt")
+    with open(path, "w") as f:
+        f.write(f"# oracle result for {g.name}, omega={omega}, delta={delta}\n")
+        f.write(f"# written by tests/golden/make_expected.py ({secs:.0f} s of oracle time)\n")
+        f.write(f"omega: {omega}\ndelta: {delta}\ncost: {res.cost}\nnum_parts: {res.num_parts}\n")
+        f.write(f"num_levels: {len(levels)}\n")
+        f.write("level_V: " + " ".join(str(v) for v in levels) + "\n")
+        f.write(f"sha_part_ids: {digest(res.part_ids.astype('<i4'))}\n")
+        f.write(f"sha_part_stats: {digest(stats.astype('<i8'))}\n")
+    print(path, res.cost, res.num_parts, len(levels), f"{secs:.0f}s")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "snn16k")
