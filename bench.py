@@ -1,0 +1,297 @@
+"""Benchmark: incidence-constrained multilevel partitioning of the 16k-node
+random SNN hypergraph (16,384 neurons, 128 pins per hyperedge, 2,097,152
+pins; Omega = 2^10 nodes, Delta = 2^12 inbound hyperedges) on GB300.
+
+One step = the whole path over one input: hgp_create (level-0 incidence
+build from the device-resident CSR) + hgp_partition (every coarsening level:
+Eq. (2) scoring with deferred checks, matching, contraction; every
+refinement level: Eq. (3) moves, in-sequence gains, prefix validity;
+projection; output) + hgp_destroy.
+
+value = level-0 pins / step time (pins/s), whole job over all ranks.
+e2e   = the same through the C ABI with pinned HOST input and output
+        buffers, the copies inside the timed region.
+The L2 (129 MB) is flushed between timed steps (the inputs are 8.4 MB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the CPU oracle (the plain single-threaded C
+restatement of the method used for parity) is timed on the host cores on a
+bounded sample of the workload family.  Multi-GPU: independent replicas
+(the method does not shard), one per rank under torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coarsening pins/s and partition wall-time at equal λ−1 cost, plain vs learned"
+OMEGA, DELTA = 1 << 10, 1 << 12
+WORKLOAD = "random SNN hypergraph, 16,384 nodes, one hyperedge per node of 128 pins (src + 127 distinct targets), 2,097,152 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0"
+SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same generator family "
+               "(32 pins per hyperedge, 65,536 pins, Omega=128, Delta=512, seed 0); the 16k-node "
+               "workload needs well over 10 minutes of oracle time on one core")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while running."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(gpu_index):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(steps=1):
+    """Times the CPU oracle on the bounded sample; returns (pins/s, seconds)."""
+    import oracle
+    import synth
+    g = synth.snn_2k(0)
+    ts = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        oracle.partition(g, 128, 512)
+        ts.append(time.perf_counter() - t)
+    return g.num_pins / statistics.median(ts), ts
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: rank 0 only, K timed steps of the bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    g = synth.snn_2k(0)
+    for _ in range(args.warmup):
+        oracle.partition(g, 128, 512)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.partition(g, 128, 512)
+        ts.append(time.perf_counter() - t)
+    tot = sum(ts)
+    value = g.num_pins * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": SAMPLE_DESC},
+            "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                             "sample": SAMPLE_DESC},
+            "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="warm up, run exactly one step, exit (for ncu launch lists)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.profile_step:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import synth
+    from paper_2604_14411_gb300 import hgp as H
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    H.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    g = synth.snn_16k(0)
+    P = g.num_pins
+    N = g.num_nodes
+    d_off = torch.from_numpy(g.offsets.copy()).to(dev)
+    d_pins = torch.from_numpy(g.pins.copy()).to(dev)
+    d_ids = torch.empty(N, dtype=torch.int32, device=dev)
+    d_pw = torch.empty(N, dtype=torch.int64, device=dev)
+    d_pin = torch.empty(N, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+
+    def step(debug=0):
+        h = H.hgp_create(N, d_off, d_pins, stream=stream)
+        try:
+            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug)
+            st = H.hgp_get_stats(h)
+        finally:
+            H.hgp_destroy(h)
+        return res, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if args.profile_step:
+        res, st = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "levels": st["num_levels"], "cost": res[0],
+                          "launches": st["kernel_launches"] + st["create_launches"]}))
+        return
+
+    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    times, stats, res = [], [], None
+    for _ in range(args.steps):
+        flush.fill_(1)                               # L2 flush, outside the timed region
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, st = step(H.HGP_DEBUG_TIMING)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        stats.append(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop(local)
+    if dist:
+        dist.barrier()
+    t_total = sum(times)
+    if dist:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    ms_per_step = t_total / args.steps
+    value = P * args.steps * world / (t_total / 1000.0)
+
+    # end to end through the C ABI with pinned host buffers
+    h_off = torch.from_numpy(g.offsets.copy()).pin_memory()
+    h_pins = torch.from_numpy(g.pins.copy()).pin_memory()
+    h_ids = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_pw = torch.empty(N, dtype=torch.int64).pin_memory()
+    h_pin = torch.empty(N, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = H.hgp_create(N, h_off.numpy(), h_pins.numpy(), stream=stream)
+        try:
+            cost, nparts, _ = H.hgp_partition(h, OMEGA, DELTA, h_ids.numpy(), h_pw.numpy(), h_pin.numpy())
+        finally:
+            H.hgp_destroy(h)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = P * world * len(e2e_times) / sum(e2e_times)
+    h2d = g.offsets.nbytes + g.pins.nbytes
+    d2h = h_ids.numel() * 4 + nparts * 8 + nparts * 4 + 8 + 4
+
+    st = stats[-1]
+    ms_score = sum(s["ms_score"] for s in stats)
+    n_score = sum(s["score_launches"] for s in stats)
+    score_bytes = sum(s["score_bytes"] for s in stats)
+    peak, peak_kind = load_peaks()
+    achieved = (score_bytes / 1e9) / (ms_score / 1000.0) if ms_score > 0 else 0.0
+    launches = int(st["kernel_launches"] + st["create_launches"])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "omega": OMEGA, "delta": DELTA, "pins": P,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "partition_ms": statistics.median(s["ms_partition"] for s in stats),
+            "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
+            "coarsening_pins_per_s": P / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
+            "refine_ms": statistics.median(s["ms_refine"] for s in stats),
+            "levels": st["num_levels"], "cost": res[0], "num_parts": res[1],
+            "gpu_launches": launches * args.steps,
+            "e2e": {"value": e2e_value, "unit": "pins/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"kernel": "k_score (Eq. 2 scoring + deferred checks)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": f"{peak_kind} (hbm copy)",
+                         "launches": int(n_score), "avg_launch_us": 1000.0 * ms_score / max(n_score, 1),
+                         "bytes_per_launch": score_bytes / max(n_score, 1)},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            v, ts = oracle_sample(steps=3)
+            line["cpu_baseline"] = {"value": v, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                                    "sample": SAMPLE_DESC + f"; median of {len(ts)} runs"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,7 @@ typedef struct {
     int64_t pins_total;        /* sum over built levels of the pin count */
     int64_t kernel_launches;   /* kernels launched by the last hgp_partition */
     int64_t moves_applied;     /* refinement moves applied, all levels */
+    int64_t create_launches;   /* kernels launched by hgp_create */
 } hgp_stats;
 
 /* Statistics of the handle's last hgp_partition (and hgp_create). */

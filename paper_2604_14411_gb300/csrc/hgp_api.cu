@@ -100,6 +100,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
         return HGP_ERR_INVALID_ARG;
     if ((flags & ~HGP_INPUT_DEVICE) != 0) return HGP_ERR_INVALID_ARG;
     double t0 = now_ms();
+    int64_t launches0 = g_launches;
     hgp_graph *g = new (std::nothrow) hgp_graph();
     if (!g) return HGP_ERR_OOM;
     g->stream = (cudaStream_t)stream;
@@ -186,6 +187,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     tmp.release_all();
     g->max_w = hmx[0];
     g->max_in = hmx[1];
+    L.max_in = hmx[1];
     int64_t W = 0;
     if (node_weights) for (int32_t x : hw) W += x;
     else W = num_nodes;
@@ -193,6 +195,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     CKC(cudaStreamSynchronize(s), "sync");
 #undef CKC
     g->stats.ms_create = now_ms() - t0;
+    g->stats.create_launches = g_launches - launches0;
     *out = g;
     return HGP_OK;
 }
@@ -432,8 +435,10 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     res->num_levels = (int32_t)levels.size();
     hgp_stats &st = g->stats;
     double ms_create = st.ms_create;
+    int64_t create_launches = st.create_launches;
     std::memset(&st, 0, sizeof(st));
     st.ms_create = ms_create;
+    st.create_launches = create_launches;
     st.num_levels = res->num_levels;
     st.num_parts = np;
     st.cost = res->cost;

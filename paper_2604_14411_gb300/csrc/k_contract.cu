@@ -66,7 +66,7 @@ __global__ void k_union(int32_t V2, const int32_t *rep_of, const int32_t *match,
                         const int32_t *ioff, const int32_t *inc, const int32_t *noff,
                         const int32_t *inn, int32_t *cntI, int32_t *cntN,
                         const int32_t *ioff2, int32_t *inc2, const int32_t *noff2,
-                        int32_t *inn2) {
+                        int32_t *inn2, int32_t *max_in) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = gw; c < V2; c += nw) {
@@ -81,7 +81,7 @@ __global__ void k_union(int32_t V2, const int32_t *rep_of, const int32_t *match,
         }
         int32_t ci = warp_union<WRITE>(Ia, nIa, Ib, nIb, WRITE ? inc2 + ioff2[c] : nullptr);
         int32_t cn = warp_union<WRITE>(Na, nNa, Nb, nNb, WRITE ? inn2 + noff2[c] : nullptr);
-        if (!WRITE && lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; }
+        if (!WRITE && lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; atomicMax(max_in, cn); }
     }
 }
 
@@ -151,8 +151,10 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     cudaError_t e;
     H.V = V2;
     H.E = L.E;
-    int32_t *rep_of = nullptr, *cntI = nullptr, *cntN = nullptr, *cntP = nullptr;
+    int32_t *rep_of = nullptr, *cntI = nullptr, *cntN = nullptr, *cntP = nullptr, *dmax = nullptr;
     e = dalloc(tmp, &rep_of, V2);
+    if (!e) e = dalloc(tmp, &dmax, 1);
+    if (!e) e = cudaMemsetAsync(dmax, 0, sizeof(int32_t), s);
     if (!e) e = dalloc(tmp, &cntI, V2);
     if (!e) e = dalloc(tmp, &cntN, V2);
     if (!e) e = dalloc(tmp, &cntP, L.E);
@@ -167,7 +169,7 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     count_launch();
     k_union<false><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
                                                   L.inn, cntI, cntN, nullptr, nullptr, nullptr,
-                                                  nullptr);
+                                                  nullptr, dmax);
     count_launch();
     k_coarse_pins<false><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
                                                          L.ioff, L.inc, cntP, nullptr, nullptr);
@@ -176,8 +178,9 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (!e) e = counts_to_offsets(tmp, cntN, H.noff, V2, s);
     if (!e) e = counts_to_offsets(tmp, cntP, H.poff, L.E, s);
     if (e) return e;
-    int32_t tot[3];
-    e = cudaMemcpyAsync(&tot[0], H.ioff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    int32_t tot[4];
+    e = cudaMemcpyAsync(&tot[3], dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&tot[0], H.ioff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[1], H.noff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[2], H.poff + L.E, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
@@ -185,13 +188,14 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (tot[0] != tot[2]) return cudaErrorInvalidValue;   // I' must be the transpose of pins'
     H.P = tot[0];
     H.Q = tot[1];
+    H.max_in = tot[3];
     e = dalloc(keep, &H.inc, H.P);
     if (!e) e = dalloc(keep, &H.inn, H.Q);
     if (!e) e = dalloc(keep, &H.pins, H.P);
     if (e) return e;
     k_union<true><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
                                                  L.inn, nullptr, nullptr, H.ioff, H.inc, H.noff,
-                                                 H.inn);
+                                                 H.inn, nullptr);
     count_launch();
     k_coarse_pins<true><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
                                                         L.ioff, L.inc, nullptr, H.poff, H.pins);

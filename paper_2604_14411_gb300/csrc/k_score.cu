@@ -7,28 +7,30 @@
 //      hyperedge with coalesced int32 loads and add omega(e) into the
 //      histogram:
 //        dense mode  -- a |N_l|-entry int32 array in shared memory,
-//                       indexed by node id (no hashing, one smem atomic
-//                       per pin visit);
+//                       indexed by node id (one smem atomic per pin visit);
 //        hash mode   -- a per-CTA open-addressing table in global memory
 //                       (levels whose node count does not fit on chip).
-//   2. Candidates are taken in the order (hist desc, id desc).  The first is
-//      found by a CTA-wide argmax and checked; if it fails, the remaining
-//      neighbours are compacted into shared memory, bitonic-sorted, and
-//      checked 1 per warp in parallel batches; the first valid one in order
-//      wins (the same answer as extracting one at a time).
+//   2. Candidates are extracted by decreasing hist value.  For the current
+//      top value h, every neighbour with hist = h is checked in parallel
+//      (one warp per candidate); the valid one of largest id wins.  If none
+//      is valid the next lower value is taken.  This visits candidates in
+//      the paper's (hist desc, id desc) order and returns the first valid
+//      one, checking a whole tie group at once.
 //   3. Check of a pair (n, m): w(n) + w(m) <= Omega, and
-//      |in(n)| + |in(m) \ in(n)| <= Delta, where membership in in(n) is a
-//      bit test in a shared-memory bitmap over E (or a binary search in the
-//      sorted in(n) when E is too large for the bitmap).  When
-//      |in(n)| + |in(m)| <= Delta the pair is valid without any test.
+//      |in(n) u in(m)| <= Delta.  When |in(n)| + |in(m)| <= Delta the pair is
+//      valid without counting.  Otherwise the union is counted either
+//        bitmap mode -- as popcount(row(n) | row(m)) over per-node bitmaps of
+//                       in() with one bit per hyperedge (row(n) staged in
+//                       shared memory, row(m) read with 16-byte loads), or
+//        list mode   -- as |in(n)| + |in(m) \ in(n)| with a binary search in
+//                       the sorted in(n), stopping as soon as Delta is
+//                       exceeded (levels whose bitmaps would not fit).
 #include "hgp_internal.cuh"
 
 namespace hgp {
 
 constexpr int kScoreThreads = 512;
 constexpr int kScoreWarps = kScoreThreads / 32;
-constexpr int kListCap = 2048;             // sorted candidate list (u64 keys)
-constexpr int kBitmapMaxEdges = 1 << 18;   // bitmap of in(n) up to 256K edges (32 KB)
 
 struct ScoreArgs {
     int32_t V, E;
@@ -36,11 +38,11 @@ struct ScoreArgs {
     int64_t omega, delta;
     int32_t *pair, *score;
     int32_t *status;
-    int32_t *gkeys, *gvals;   // hash mode: per-CTA tables of gcap entries
+    int32_t *gkeys, *gvals;          // hash mode: per-CTA tables of gcap entries
     int32_t gcap;
     unsigned long long *bytes;
-    int32_t use_bitmap;
-    int32_t bm_words;
+    const uint32_t *bm;              // bitmap mode: [V][bm_words] rows of in()
+    int32_t bm_words;                // multiple of 4 (16-byte rows); 0 = list mode
 };
 
 __device__ __forceinline__ uint32_t hash_u32(uint32_t x) {
@@ -48,53 +50,54 @@ __device__ __forceinline__ uint32_t hash_u32(uint32_t x) {
     return x;
 }
 
-template <typename T>
-__device__ T block_max_u64(T v, T *red) {
+__device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        T y = __shfl_xor_sync(0xffffffffu, v, o);
-        v = y > v ? y : v;
-    }
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     if (lane_id() == 0) red[warp_id()] = v;
     __syncthreads();
-    T r = 0;
-    for (int i = 0; i < kScoreWarps; ++i) r = red[i] > r ? red[i] : r;
-    return r;
-}
-
-__device__ int32_t block_sum_i32(int32_t v, int32_t *red) {
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane_id() == 0) red[warp_id()] = v;
-    __syncthreads();
-    int32_t r = 0;
-    for (int i = 0; i < kScoreWarps; ++i) r += red[i];
+    int32_t r = red[0];
+#pragma unroll
+    for (int i = 1; i < kScoreWarps; ++i) r = max(r, red[i]);
     return r;
 }
 
 // Warp-cooperative validity test of pair (n, m); all lanes return the same.
-__device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, const uint32_t *bm,
-                           unsigned long long &bytes) {
+__device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, const uint32_t *row_n,
+                           int64_t in_n, unsigned long long &bytes) {
     if ((int64_t)a.w[n] + a.w[m] > a.omega) return false;
-    int32_t n0 = a.noff[n], n1 = a.noff[n + 1];
     int32_t m0 = a.noff[m], m1 = a.noff[m + 1];
-    int64_t in_n = n1 - n0, in_m = m1 - m0;
+    int64_t in_m = m1 - m0;
     if (in_n + in_m <= a.delta) return true;
+    if (a.bm_words) {
+        const uint4 *rm = reinterpret_cast<const uint4 *>(a.bm + (int64_t)m * a.bm_words);
+        const uint4 *rn = reinterpret_cast<const uint4 *>(row_n);
+        int32_t q = a.bm_words >> 2;
+        int32_t u = 0;
+        for (int32_t i = lane_id(); i < q; i += 32) {
+            uint4 x = rm[i], y = rn[i];
+            u += __popc(x.x | y.x) + __popc(x.y | y.y) + __popc(x.z | y.z) + __popc(x.w | y.w);
+        }
+        u = warp_sum(u);
+        if (lane_id() == 0) bytes += 4ull * (unsigned long long)a.bm_words;
+        return u <= a.delta;
+    }
+    int32_t n0 = a.noff[n], n1 = a.noff[n + 1];
     int64_t room = a.delta - in_n;          // edges of in(m) allowed outside in(n)
     int64_t extra = 0;
-    for (int32_t base = m0; base < m1; base += 32) {
-        int32_t j = base + lane_id();
+    int32_t seen = 0;
+    for (int32_t base = m0; base < m1; base += 128) {
         int32_t miss = 0;
-        if (j < m1) {
-            int32_t e = a.inn[j];
-            bool member = bm ? ((bm[e >> 5] >> (e & 31)) & 1u) : contains_sorted(a.inn, n0, n1, e);
-            miss = member ? 0 : 1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int32_t j = base + u * 32 + lane_id();
+            if (j < m1) miss += contains_sorted(a.inn, n0, n1, a.inn[j]) ? 0 : 1;
         }
-        extra += __popc(__ballot_sync(0xffffffffu, miss));
+        extra += warp_sum(miss);
+        seen += min(128, m1 - base);
         if (extra > room) break;
     }
-    if (lane_id() == 0) bytes += 4ull * (unsigned long long)(m1 - m0);
+    if (lane_id() == 0) bytes += 4ull * (unsigned long long)seen;
     return extra <= room;
 }
 
@@ -102,15 +105,10 @@ template <bool DENSE>
 __global__ void __launch_bounds__(kScoreThreads)
 k_score(ScoreArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: [bitmap words][u64 list kListCap][dense hist V]
-    uint32_t *bm = reinterpret_cast<uint32_t *>(smem);
-    unsigned long long *list =
-        reinterpret_cast<unsigned long long *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
-    int32_t *hist = reinterpret_cast<int32_t *>(list + kListCap);
-    __shared__ unsigned long long red64[kScoreWarps];
-    __shared__ int32_t red32[kScoreWarps];
-    __shared__ int32_t s_cnt, s_found, s_bm_ready;
-    __shared__ int32_t s_wvalid[kScoreWarps];
+    // layout: [row of in(n): bm_words][dense hist V]
+    uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
+    int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
+    __shared__ int32_t red[kScoreWarps];
 
     int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
     int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
@@ -119,12 +117,16 @@ k_score(ScoreArgs a) {
     unsigned long long bytes = 0;
 
     for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
-        // ---- clear ----
+        // ---- clear; stage row(n) ----
         for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
             if (DENSE) hist[i] = 0;
             else { gkeys[i] = -1; gvals[i] = 0; }
         }
-        if (threadIdx.x == 0) s_bm_ready = 0;
+        if (a.bm_words) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.bm + (int64_t)n * a.bm_words);
+            uint4 *dst = reinterpret_cast<uint4 *>(row_n);
+            for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
+        }
         __syncthreads();
         // ---- Eq. (2) accumulation ----
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
@@ -152,147 +154,50 @@ k_score(ScoreArgs a) {
                 bytes += 16ull + 4ull * (unsigned long long)(p1 - p0);  // inc, omega, 2 offsets, pins
         }
         __syncthreads();
-        // ---- first candidate: CTA-wide argmax of (hist, id) ----
-        unsigned long long mx = 0;
-        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
-            int32_t h, m;
-            if (DENSE) { h = hist[i]; m = i; }
-            else { m = gkeys[i]; h = m >= 0 ? gvals[i] : 0; }
-            if (h > 0) {
-                unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)m;
-                mx = key > mx ? key : mx;
+        // ---- extraction by decreasing hist value ----
+        int64_t in_n = a.noff[n + 1] - a.noff[n];
+        int32_t hcur = 0x7fffffff, result = -1, rscore = 0;
+        for (;;) {
+            int32_t hm = 0;
+            for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+                int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
+                if (h < hcur && h > hm) hm = h;
             }
-        }
-        unsigned long long best = block_max_u64(mx, red64);
-        int32_t result = -1, rscore = 0;
-        if (best != 0) {
-            int32_t m = (int32_t)(best & 0xffffffffu);
-            // the bitmap is needed only if some check must count the union
-            int64_t in_n = a.noff[n + 1] - a.noff[n];
-            int64_t in_m = a.noff[m + 1] - a.noff[m];
-            bool need_bm = a.use_bitmap && (in_n + in_m > a.delta);
-            if (need_bm) {
-                for (int32_t i = threadIdx.x; i < a.bm_words; i += kScoreThreads) bm[i] = 0u;
-                __syncthreads();
-                for (int32_t j = a.noff[n] + threadIdx.x; j < a.noff[n + 1]; j += kScoreThreads) {
-                    int32_t e = a.inn[j];
-                    atomicOr(&bm[e >> 5], 1u << (e & 31));
+            int32_t hmax = block_max_i32(hm, red);
+            if (hmax == 0) break;
+            // every neighbour with hist == hmax, one warp per candidate
+            int32_t best_id = -1;
+            int32_t per_warp = (((cap + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+            int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
+            if (DENSE) {
+                // ids are table indices: scan downwards, the first valid is this warp's best
+                for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
+                    int32_t i = base + lane_id();
+                    bool hit = i < hi && hist[i] == hmax;
+                    unsigned ball = __ballot_sync(0xffffffffu, hit);
+                    while (ball && best_id < 0) {
+                        int src = 31 - __clz(ball);
+                        ball &= ~(1u << src);
+                        if (warp_check(a, n, base + src, row_n, in_n, bytes)) best_id = base + src;
+                    }
                 }
-                if (threadIdx.x == 0) s_bm_ready = 1;
-                __syncthreads();
-            }
-            if (warp_id() == 0) {
-                bool ok = warp_check(a, n, m, a.use_bitmap ? bm : nullptr, bytes);
-                if (lane_id() == 0) s_found = ok ? 1 : 0;
-            }
-            __syncthreads();
-            if (s_found) {
-                result = m;
-                rscore = (int32_t)(best >> 32);
             } else {
-                // ---- remaining candidates, in order ----
-                if (a.use_bitmap && !s_bm_ready) {
-                    for (int32_t i = threadIdx.x; i < a.bm_words; i += kScoreThreads) bm[i] = 0u;
-                    __syncthreads();
-                    for (int32_t j = a.noff[n] + threadIdx.x; j < a.noff[n + 1]; j += kScoreThreads) {
-                        int32_t e = a.inn[j];
-                        atomicOr(&bm[e >> 5], 1u << (e & 31));
-                    }
-                    __syncthreads();
-                }
-                int32_t cnt_local = 0;
-                for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
-                    int32_t h, mm;
-                    if (DENSE) { h = hist[i]; mm = i; }
-                    else { mm = gkeys[i]; h = mm >= 0 ? gvals[i] : 0; }
-                    if (h > 0) {
-                        unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)mm;
-                        cnt_local += key < best ? 1 : 0;
-                    }
-                }
-                int32_t cnt = block_sum_i32(cnt_local, red32);
-                if (cnt <= kListCap) {
-                    // compact, pad, bitonic sort (descending), check in batches
-                    if (threadIdx.x == 0) s_cnt = 0;
-                    __syncthreads();
-                    for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
-                        int32_t h, mm;
-                        if (DENSE) { h = hist[i]; mm = i; }
-                        else { mm = gkeys[i]; h = mm >= 0 ? gvals[i] : 0; }
-                        if (h > 0) {
-                            unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)mm;
-                            if (key < best) list[atomicAdd(&s_cnt, 1)] = key;
-                        }
-                    }
-                    __syncthreads();
-                    int32_t len = 1;
-                    while (len < cnt) len <<= 1;
-                    for (int32_t i = cnt + threadIdx.x; i < len; i += kScoreThreads) list[i] = 0ull;
-                    __syncthreads();
-                    for (int32_t k = 2; k <= len; k <<= 1) {
-                        for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                            for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) {
-                                int32_t ixj = i ^ jj;
-                                if (ixj > i) {
-                                    unsigned long long x = list[i], y = list[ixj];
-                                    bool desc = (i & k) == 0;
-                                    if (desc ? (x < y) : (x > y)) { list[i] = y; list[ixj] = x; }
-                                }
-                            }
-                            __syncthreads();
-                        }
-                    }
-                    for (int32_t b = 0; b < cnt; b += kScoreWarps) {
-                        int32_t idx = b + warp_id();
-                        bool ok = false;
-                        if (idx < cnt) {
-                            int32_t mm = (int32_t)(list[idx] & 0xffffffffu);
-                            ok = warp_check(a, n, mm, a.use_bitmap ? bm : nullptr, bytes);
-                        }
-                        if (lane_id() == 0) s_wvalid[warp_id()] = ok ? 1 : 0;
-                        __syncthreads();
-                        int32_t first = -1;
-                        for (int q = 0; q < kScoreWarps; ++q)
-                            if (s_wvalid[q]) { first = q; break; }
-                        __syncthreads();
-                        if (first >= 0) {
-                            unsigned long long key = list[b + first];
-                            result = (int32_t)(key & 0xffffffffu);
-                            rscore = (int32_t)(key >> 32);
-                            break;
-                        }
-                    }
-                } else {
-                    // many candidates: one extraction per round (same order)
-                    unsigned long long thr = best;
-                    for (int32_t round = 0; round < cnt; ++round) {
-                        unsigned long long lm = 0;
-                        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
-                            int32_t h, mm;
-                            if (DENSE) { h = hist[i]; mm = i; }
-                            else { mm = gkeys[i]; h = mm >= 0 ? gvals[i] : 0; }
-                            if (h > 0) {
-                                unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)mm;
-                                if (key < thr && key > lm) lm = key;
-                            }
-                        }
-                        unsigned long long nb = block_max_u64(lm, red64);
-                        if (nb == 0) break;
-                        if (warp_id() == 0) {
-                            bool ok = warp_check(a, n, (int32_t)(nb & 0xffffffffu),
-                                                 a.use_bitmap ? bm : nullptr, bytes);
-                            if (lane_id() == 0) s_found = ok ? 1 : 0;
-                        }
-                        __syncthreads();
-                        if (s_found) {
-                            result = (int32_t)(nb & 0xffffffffu);
-                            rscore = (int32_t)(nb >> 32);
-                            break;
-                        }
-                        thr = nb;
+                for (int32_t base = lo; base < hi; base += 32) {
+                    int32_t i = base + lane_id();
+                    int32_t m = -1;
+                    if (i < hi && gkeys[i] >= 0 && gvals[i] == hmax) m = gkeys[i];
+                    unsigned ball = __ballot_sync(0xffffffffu, m >= 0);
+                    while (ball) {
+                        int src = __ffs(ball) - 1;
+                        ball &= ball - 1;
+                        int32_t cm = __shfl_sync(0xffffffffu, m, src);
+                        if (cm > best_id && warp_check(a, n, cm, row_n, in_n, bytes)) best_id = cm;
                     }
                 }
             }
+            int32_t win = block_max_i32(best_id, red);
+            if (win >= 0) { result = win; rscore = hmax; break; }
+            hcur = hmax;
         }
         if (threadIdx.x == 0) {
             a.pair[n] = result;
@@ -324,16 +229,22 @@ __global__ void k_max_work(int32_t V, const int32_t *ioff, const int32_t *inc, c
     }
 }
 
-struct ScoreLaunch {
-    bool dense;
-    size_t smem;
-    int blocks;
-};
-
-static size_t score_smem(bool dense, int32_t V, int32_t bm_words) {
-    return sizeof(uint32_t) * (size_t)bm_words + sizeof(unsigned long long) * kListCap +
-           (dense ? sizeof(int32_t) * (size_t)V : 0);
+// Rows of in(): bit e of row n is set iff e in in(n).
+__global__ void k_in_bitmap(int32_t V, const int32_t *noff, const int32_t *inn, int32_t words,
+                            uint32_t *bm) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        uint32_t *row = bm + n * words;
+        for (int32_t j = noff[n] + lane_id(); j < noff[n + 1]; j += 32) {
+            int32_t e = inn[j];
+            atomicOr(&row[e >> 5], 1u << (e & 31));
+        }
+    }
 }
+
+constexpr int64_t kBitmapBudget = 1ll << 30;   // bytes of in() bitmaps per level
+constexpr int32_t kBitmapMaxWords = 8192;       // 32 KB row in shared memory
 
 cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
                       int32_t *pair, int32_t *score, int32_t *status,
@@ -349,24 +260,38 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     a.noff = L.noff; a.inn = L.inn; a.ew = ew;
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score; a.status = status; a.bytes = bytes;
-    a.use_bitmap = (L.E <= kBitmapMaxEdges && !(debug & HGP_DEBUG_NO_BITMAP)) ? 1 : 0;
-    a.bm_words = a.use_bitmap ? (((L.E + 31) / 32 + 3) & ~3) : 0;   // keeps the u64 list 16-byte aligned
-    // static smem of the kernel is small (< 1 KB); keep 2 KB of headroom
-    size_t dense_smem = score_smem(true, L.V, a.bm_words);
-    bool dense = dense_smem + 2048 <= (size_t)max_smem && !(debug & HGP_DEBUG_FORCE_GLOBAL);
-    size_t smem = dense ? dense_smem : score_smem(false, L.V, a.bm_words);
-    int sms = num_sms();
-    int blocks = 0;
     cudaError_t e;
+    // bitmaps only when some pair may need a union count
+    int32_t words = ((L.E + 31) / 32 + 3) & ~3;
+    bool need_union = 2 * (int64_t)L.max_in > delta;
+    if (need_union && !(debug & HGP_DEBUG_NO_BITMAP) && words <= kBitmapMaxWords &&
+        (int64_t)L.V * words * 4 <= kBitmapBudget) {
+        uint32_t *bm = nullptr;
+        e = dalloc(ar, &bm, (size_t)L.V * words);
+        if (e) return e;
+        e = cudaMemsetAsync(bm, 0, sizeof(uint32_t) * (size_t)L.V * words, s);
+        if (e) return e;
+        int blocks = div_up((int64_t)L.V * 32, 256);
+        if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+        k_in_bitmap<<<blocks, 256, 0, s>>>(L.V, L.noff, L.inn, words, bm);
+        count_launch();
+        a.bm = bm;
+        a.bm_words = words;
+    }
+    size_t row_bytes = sizeof(uint32_t) * (size_t)a.bm_words;
+    size_t dense_smem = row_bytes + sizeof(int32_t) * (size_t)L.V;
+    bool dense = dense_smem + 2048 <= (size_t)max_smem && !(debug & HGP_DEBUG_FORCE_GLOBAL);
+    int sms = num_sms();
     if (dense) {
-        e = cudaFuncSetAttribute(k_score<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_score<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dense_smem);
         if (e) return e;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, dense_smem);
         if (per_sm < 1) per_sm = 1;
-        blocks = sms * per_sm;
+        int blocks = sms * per_sm;
         if (blocks > L.V) blocks = L.V;
-        k_score<true><<<blocks, kScoreThreads, smem, s>>>(a);
+        k_score<true><<<blocks, kScoreThreads, dense_smem, s>>>(a);
         count_launch();
         return cudaGetLastError();
     }
@@ -387,14 +312,14 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     while (gcap < 2 * distinct) gcap <<= 1;
     if (gcap > (1ull << 30)) return cudaErrorMemoryAllocation;
     a.gcap = (int32_t)gcap;
-    e = cudaFuncSetAttribute(k_score<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_score<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_bytes);
     if (e) return e;
-    blocks = sms * 2;
+    int blocks = sms * 2;
     if (blocks > L.V) blocks = L.V;
     e = dalloc(ar, &a.gkeys, (size_t)blocks * gcap);
     if (!e) e = dalloc(ar, &a.gvals, (size_t)blocks * gcap);
     if (e) return e;
-    k_score<false><<<blocks, kScoreThreads, smem, s>>>(a);
+    k_score<false><<<blocks, kScoreThreads, row_bytes, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
