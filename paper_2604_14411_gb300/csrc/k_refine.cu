@@ -32,7 +32,7 @@ namespace hgp {
 
 constexpr int kPropThreads = 256;
 constexpr int kPropWarps = kPropThreads / 32;
-constexpr int kPartsDenseMax = 16384;
+constexpr int kPartsDenseMax = 12288;   // pres + touched list: 96 KB of smem
 
 static int grid1d(int64_t n) {
     int b = div_up(n, 256);
@@ -157,11 +157,15 @@ struct PropArgs {
 
 template <bool DENSE>
 __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
-    extern __shared__ __align__(16) int32_t pres_s[];
+    extern __shared__ __align__(16) int32_t smem_p[];
     __shared__ unsigned long long red64[kPropWarps];
     __shared__ long long red_s[kPropWarps], red_w[kPropWarps];
-    int32_t *pres = DENSE ? pres_s : a.gpres + (int64_t)blockIdx.x * a.K;
+    __shared__ int32_t s_nt;
+    // pres(n, p) per part, and the list of parts touched for this node
+    int32_t *pres = DENSE ? smem_p : a.gpres + (int64_t)blockIdx.x * 2 * a.K;
+    int32_t *touched = pres + a.K;
     for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
+    if (threadIdx.x == 0) s_nt = 0;
     __syncthreads();
     for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
         int32_t ps = a.rho[n];
@@ -174,8 +178,11 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
             if (lane_id() == 0) wI += we;
             for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
                 int32_t p = a.rpart[q];
-                if (p == ps) { if (a.rcnt[q] == 1) sav += we; }
-                else atomicAdd(&pres[p], we);
+                if (p == ps) {
+                    if (a.rcnt[q] == 1) sav += we;
+                } else if (atomicAdd(&pres[p], we) == 0) {
+                    touched[atomicAdd(&s_nt, 1)] = p;
+                }
             }
         }
         sav = warp_sum(sav);
@@ -183,18 +190,15 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         if (lane_id() == 0) { red_s[warp_id()] = sav; red_w[warp_id()] = wI; }
         __syncthreads();
         // best admissible part: max pres, ties to the smaller id
-        unsigned long long best = 0;
+        int32_t nt = s_nt;
         int32_t wn = a.w[n];
-        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
-            int32_t e = a.inc[k];
-            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
-            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
-                int32_t p = a.rpart[q];
-                if (p != ps && (int64_t)a.size[p] + wn <= a.omega) {
-                    unsigned long long key = ((unsigned long long)(uint32_t)pres[p] << 32) |
-                                             (uint32_t)(0x7fffffff - p);
-                    best = key > best ? key : best;
-                }
+        unsigned long long best = 0;
+        for (int32_t t = threadIdx.x; t < nt; t += kPropThreads) {
+            int32_t p = touched[t];
+            if ((int64_t)a.size[p] + wn <= a.omega) {
+                unsigned long long key = ((unsigned long long)(uint32_t)pres[p] << 32) |
+                                         (uint32_t)(0x7fffffff - p);
+                best = key > best ? key : best;
             }
         }
 #pragma unroll
@@ -204,15 +208,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         }
         if (lane_id() == 0) red64[warp_id()] = best;
         __syncthreads();
-        // clear the touched entries
-        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
-            int32_t e = a.inc[k];
-            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
-            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
-                int32_t p = a.rpart[q];
-                if (p != ps) pres[p] = 0;
-            }
-        }
+        for (int32_t t = threadIdx.x; t < nt; t += kPropThreads) pres[touched[t]] = 0;
         if (threadIdx.x == 0) {
             unsigned long long b = 0;
             long long S = 0, W = 0;
@@ -229,6 +225,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
             }
             a.gain[n] = g;
             a.pd[n] = pd;
+            s_nt = 0;
         }
         __syncthreads();
     }
@@ -267,66 +264,94 @@ __device__ __forceinline__ void run_lookup(const int32_t *rpart, const int32_t *
     else { c = 0; ci = 0; }
 }
 
-struct SeqArgs {
-    int32_t M;
-    const int32_t *mv_n, *mv_ps, *mv_pd, *idx_of;
-    const int32_t *ioff, *inc, *poff, *pins, *ew, *src;
-    const uint8_t *sdst;
-    const int32_t *rpart, *rcnt, *rcin, *nrun;
-    int32_t *gseq, *lose_in, *gain_in;
-};
+// In-sequence gains from per-(edge, part) events.  Move k emits, for every
+// e in I(n_k), a "leave" event on (e, ps_k) and an "enter" event on
+// (e, pd_k), both tagged with k and with whether n_k is a destination of e.
+// Stably sorted by (e, part) the events of one pair are in move order, so a
+// segmented prefix sum gives pins(p, e) and pins_in(p, e) just before each
+// move; the exact Eq. (1) change of the move and its inbound-set changes
+// follow from those counts (== 1 when leaving, == 0 when entering).
+__global__ void k_move_deg(int32_t M, const int32_t *mv_n, const int32_t *ioff, int32_t *deg) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = mv_n[k];
+        deg[k] = 2 * (ioff[n + 1] - ioff[n]);
+    }
+}
 
-__global__ void __launch_bounds__(kPropThreads) k_seq_gain(SeqArgs a) {
-    __shared__ long long red[3][kPropWarps];
-    for (int32_t k = blockIdx.x; k < a.M; k += gridDim.x) {
-        int32_t n = a.mv_n[k], ps = a.mv_ps[k], pd = a.mv_pd[k];
-        long long g = 0, lose = 0, gainin = 0;
-        for (int32_t t = a.ioff[n] + warp_id(); t < a.ioff[n + 1]; t += kPropWarps) {
-            int32_t e = a.inc[t];
-            int32_t p0 = a.poff[e], p1 = a.poff[e + 1];
-            int32_t se = a.src[e];
-            bool sd = a.sdst[e] != 0;
-            int32_t dcs = 0, dcd = 0, dcsi = 0, dcdi = 0;
-            for (int32_t j = p0 + lane_id(); j < p1; j += 32) {
-                int32_t m = a.pins[j];
-                if (m == n) continue;
-                int32_t km = a.idx_of[m];
-                if (km < 0 || km >= k) continue;
-                int32_t pm_s = a.mv_ps[km], pm_d = a.mv_pd[km];
-                int32_t ds = (pm_d == ps) - (pm_s == ps);
-                int32_t dd = (pm_d == pd) - (pm_s == pd);
-                dcs += ds;
-                dcd += dd;
-                if (m != se || sd) { dcsi += ds; dcdi += dd; }
-            }
-            dcs = warp_sum(dcs);
-            dcd = warp_sum(dcd);
-            dcsi = warp_sum(dcsi);
-            dcdi = warp_sum(dcdi);
-            if (lane_id() == 0) {
-                int32_t r0 = p0, r1 = p0 + a.nrun[e];
-                int32_t cs, csi, cd, cdi;
-                run_lookup(a.rpart, a.rcnt, a.rcin, r0, r1, ps, cs, csi);
-                run_lookup(a.rpart, a.rcnt, a.rcin, r0, r1, pd, cd, cdi);
-                cs += dcs; cd += dcd; csi += dcsi; cdi += dcdi;
-                int32_t we = a.ew[e];
-                g += (long long)we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
-                if (n != se || sd) {        // e is inbound to n
-                    lose += (csi == 1) ? 1 : 0;
-                    gainin += (cdi == 0) ? 1 : 0;
-                }
-            }
+__global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_ps,
+                             const int32_t *mv_pd, const int32_t *ioff, const int32_t *inc,
+                             const int32_t *src, const uint8_t *sdst, const int32_t *evoff,
+                             uint32_t *ev_p, int32_t *ev_e, int32_t *ev_k, uint8_t *ev_dst,
+                             int32_t *ev_id) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = gw; k < M; k += nw) {
+        int32_t n = mv_n[k], ps = mv_ps[k], pd = mv_pd[k];
+        int32_t base = evoff[k], i0 = ioff[n], d = ioff[n + 1] - i0;
+        for (int32_t t = lane_id(); t < d; t += 32) {
+            int32_t e = inc[i0 + t];
+            uint8_t isdst = (n != src[e] || sdst[e]) ? 1 : 0;
+            int32_t j = base + 2 * t;
+            ev_p[j] = (uint32_t)ps;  ev_e[j] = e; ev_k[j] = (int32_t)k; ev_dst[j] = isdst; ev_id[j] = j;
+            ev_p[j + 1] = (uint32_t)pd; ev_e[j + 1] = e; ev_k[j + 1] = (int32_t)k; ev_dst[j + 1] = isdst;
+            ev_id[j + 1] = j + 1;
         }
-        if (lane_id() == 0) { red[0][warp_id()] = g; red[1][warp_id()] = lose; red[2][warp_id()] = gainin; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long G = 0, Lo = 0, Gi = 0;
-            for (int q = 0; q < kPropWarps; ++q) { G += red[0][q]; Lo += red[1][q]; Gi += red[2][q]; }
-            a.gseq[k] = (int32_t)G;
-            a.lose_in[k] = (int32_t)Lo;
-            a.gain_in[k] = (int32_t)Gi;
+    }
+}
+
+__global__ void k_gather_u32(int64_t n, const int32_t *src, const int32_t *idx, uint32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (uint32_t)src[idx[i]];
+}
+
+// after the sorts: part of each event and the +-1 deltas (events at even ids
+// leave, at odd ids enter)
+__global__ void k_seq_prep(int64_t nev, const int32_t *jS, const uint32_t *ev_p,
+                           const uint8_t *ev_dst, int32_t *pS, int32_t *d_all, int32_t *d_in) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t j = jS[i];
+        int32_t d = (j & 1) ? 1 : -1;
+        pS[i] = (int32_t)ev_p[j];
+        d_all[i] = d;
+        d_in[i] = ev_dst[j] ? d : 0;
+    }
+}
+
+__global__ void k_seq_apply(int64_t nev, const uint32_t *eS, const int32_t *pS, const int32_t *jS,
+                            const int32_t *pre_all, const int32_t *pre_in, const int32_t *ev_k,
+                            const uint8_t *ev_dst, const int32_t *poff, const int32_t *nrun,
+                            const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
+                            const int32_t *ew, int32_t *gseq, int32_t *lose_in, int32_t *gain_in) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = eS[i];
+        int32_t p = pS[i];
+        // first event of the same (e, p) group
+        int64_t lo = 0, hi = i;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            bool less = eS[mid] < e || (eS[mid] == e && pS[mid] < p);
+            if (less) lo = mid + 1; else hi = mid;
         }
-        __syncthreads();
+        int32_t r0 = poff[e], r1 = r0 + nrun[e];
+        int32_t q = lower_bound_i32(rpart, r0, r1, p);
+        int32_t c0 = 0, c0in = 0;
+        if (q < r1 && rpart[q] == p) { c0 = rcnt[q]; c0in = rcin[q]; }
+        int32_t c = c0 + pre_all[i] - pre_all[lo];
+        int32_t ci = c0in + pre_in[i] - pre_in[lo];
+        int32_t j = jS[i];
+        int32_t k = ev_k[j];
+        bool dst = ev_dst[j] != 0;
+        if ((j & 1) == 0) {                                  // leaves ps
+            if (c == 1) atomicAdd(&gseq[k], ew[e]);
+            if (dst && ci == 1) atomicAdd(&lose_in[k], 1);
+        } else {                                             // enters pd
+            if (c == 0) atomicAdd(&gseq[k], -ew[e]);
+            if (dst && ci == 0) atomicAdd(&gain_in[k], 1);
+        }
     }
 }
 
@@ -492,7 +517,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     pa.nrun = R.nrun; pa.omega = omega; pa.gain = pg; pa.pd = ppd;
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
-        size_t smem = sizeof(int32_t) * (size_t)K;
+        size_t smem = 2 * sizeof(int32_t) * (size_t)K;
         e = cudaFuncSetAttribute(k_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return e;
         int per_sm = 0;
@@ -504,7 +529,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     } else {
         int blocks = sms * 4;
         if (blocks > V) blocks = V;
-        e = dalloc(tmp, &pa.gpres, (size_t)blocks * K);
+        e = dalloc(tmp, &pa.gpres, (size_t)blocks * 2 * K);
         if (e) return e;
         k_propose<false><<<blocks, kPropThreads, 0, s>>>(pa);
     }
@@ -545,15 +570,61 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     fill_i32(idx_of, -1, V, s);
     k_move_info<<<grid1d(M), 256, 0, s>>>(M, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
     count_launch();
-    SeqArgs sa{};
-    sa.M = M; sa.mv_n = mv_n; sa.mv_ps = mv_ps; sa.mv_pd = mv_pd; sa.idx_of = idx_of;
-    sa.ioff = L.ioff; sa.inc = L.inc; sa.poff = L.poff; sa.pins = L.pins; sa.ew = ew;
-    sa.src = L.src; sa.sdst = L.sdst; sa.rpart = R.rpart; sa.rcnt = R.rcnt; sa.rcin = R.rcin;
-    sa.nrun = R.nrun; sa.gseq = gseq; sa.lose_in = lose; sa.gain_in = gin;
+    // in-sequence gains from per-(edge, part) events
     {
-        int blocks = sms * 8;
-        if (blocks > M) blocks = M;
-        k_seq_gain<<<blocks, kPropThreads, 0, s>>>(sa);
+        int32_t *deg, *evoff, *dNev;
+        e = dalloc(tmp, &deg, M);
+        if (!e) e = dalloc(tmp, &evoff, (size_t)M + 1);
+        if (e) return e;
+        k_move_deg<<<grid1d(M), 256, 0, s>>>(M, mv_n, L.ioff, deg);
+        count_launch();
+        e = counts_to_offsets(tmp, deg, evoff, M, s);
+        if (e) return e;
+        dNev = evoff + M;
+        int32_t hnev = 0;
+        e = cudaMemcpyAsync(&hnev, dNev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return e;
+        int64_t nq = hnev;
+        uint32_t *ev_p, *p1, *e1, *eS;
+        int32_t *ev_e, *ev_k, *ev_id, *j1, *jS, *pS, *d_all, *d_in, *pre_all, *pre_in;
+        uint8_t *ev_dst;
+        e = dalloc(tmp, &ev_p, nq);
+        if (!e) e = dalloc(tmp, &ev_e, nq);
+        if (!e) e = dalloc(tmp, &ev_k, nq);
+        if (!e) e = dalloc(tmp, &ev_dst, nq);
+        if (!e) e = dalloc(tmp, &ev_id, nq);
+        if (!e) e = dalloc(tmp, &p1, nq);
+        if (!e) e = dalloc(tmp, &j1, nq);
+        if (!e) e = dalloc(tmp, &e1, nq);
+        if (!e) e = dalloc(tmp, &eS, nq);
+        if (!e) e = dalloc(tmp, &jS, nq);
+        if (!e) e = dalloc(tmp, &pS, nq);
+        if (!e) e = dalloc(tmp, &d_all, nq);
+        if (!e) e = dalloc(tmp, &d_in, nq);
+        if (!e) e = dalloc(tmp, &pre_all, nq);
+        if (!e) e = dalloc(tmp, &pre_in, nq);
+        if (e) return e;
+        k_seq_events<<<grid_warps(M), 256, 0, s>>>(M, mv_n, mv_ps, mv_pd, L.ioff, L.inc, L.src,
+                                                   L.sdst, evoff, ev_p, ev_e, ev_k, ev_dst, ev_id);
+        count_launch();
+        // stable by part, then stable by edge: grouped by (e, p), move order inside
+        e = radix_sort_pairs(tmp, ev_p, ev_id, p1, j1, nq, bits_for(K > 0 ? K - 1 : 0), s);
+        if (e) return e;
+        k_gather_u32<<<grid1d(nq), 256, 0, s>>>(nq, ev_e, j1, e1);
+        count_launch();
+        e = radix_sort_pairs(tmp, e1, j1, eS, jS, nq, bits_for(L.E > 0 ? L.E - 1 : 0), s);
+        if (e) return e;
+        k_seq_prep<<<grid1d(nq), 256, 0, s>>>(nq, jS, ev_p, ev_dst, pS, d_all, d_in);
+        count_launch();
+        e = exclusive_scan_i32(tmp, d_all, pre_all, nq, nullptr, s);
+        if (!e) e = exclusive_scan_i32(tmp, d_in, pre_in, nq, nullptr, s);
+        if (e) return e;
+        cudaMemsetAsync(gseq, 0, sizeof(int32_t) * (size_t)M, s);
+        cudaMemsetAsync(lose, 0, sizeof(int32_t) * (size_t)M, s);
+        cudaMemsetAsync(gin, 0, sizeof(int32_t) * (size_t)M, s);
+        k_seq_apply<<<grid1d(nq), 256, 0, s>>>(nq, eS, pS, jS, pre_all, pre_in, ev_k, ev_dst, L.poff,
+                                               R.nrun, R.rpart, R.rcnt, R.rcin, ew, gseq, lose, gin);
         count_launch();
     }
     // prefix validity from per-part events
