@@ -16,7 +16,8 @@ cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *
                       int32_t *match, int32_t *gamma, int32_t *d_V2, int32_t *status,
                       cudaStream_t s);
 cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
-                         int32_t *status, cudaStream_t s);
+                         const int32_t *pair, const int32_t *score, int32_t *status,
+                         cudaStream_t s);
 int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
                      cudaError_t *cerr, std::string *why, cudaStream_t s);
 struct RefineOut {
@@ -352,7 +353,7 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
             }
             Level H;
             tm.start(2, &ev_a);
-            CKP(run_contract(lv, tmp, L, V2, H, d_status, s), "contract");
+            CKP(run_contract(lv, tmp, L, V2, H, pair, score, d_status, s), "contract");
             tm.stop(2, ev_a);
             levels.push_back(H);
             pins_total += H.P;

@@ -38,6 +38,17 @@ struct Level {
     uint8_t *sdst = nullptr;
     int32_t *gamma = nullptr;   // [V] map to level+1 (when this level was contracted)
     int32_t *match = nullptr;   // [V]
+    // carried from the previous level's scoring (null at level 0):
+    //   dead[n]   n had no valid candidate one level down; validity only shrinks
+    //             under merging, so n has none now and is no one's candidate
+    //   merged[n] n is a pair formed by the last matching
+    //   thr[n]    (score << 32 | id) of n's previous candidate, in previous-level
+    //             ids, for unmerged n (0 otherwise): every unmerged neighbour
+    //             ranked above it was already found invalid
+    //   old_id[n] previous-level id of n's smaller member
+    uint8_t *dead = nullptr, *merged = nullptr;
+    unsigned long long *thr = nullptr;
+    int32_t *old_id = nullptr;
 };
 
 // ---------------- stream-ordered device memory ----------------

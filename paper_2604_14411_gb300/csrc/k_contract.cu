@@ -120,6 +120,24 @@ __global__ void k_coarse_pins(int32_t E, const int32_t *poff, const int32_t *pin
     }
 }
 
+// State carried into the next level's scoring (see Level::dead/merged/thr).
+__global__ void k_carry(int32_t V, const int32_t *pair, const int32_t *score, const int32_t *match,
+                        const int32_t *gamma, const uint8_t *dead, uint8_t *dead2, uint8_t *merged2,
+                        unsigned long long *thr2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = (int32_t)i, m = match[n], c = gamma[n];
+        if (m != n) {
+            if (m > n) { merged2[c] = 1; dead2[c] = 0; thr2[c] = 0ull; }
+        } else {
+            merged2[c] = 0;
+            bool d = pair[n] < 0 || (dead && dead[n]);
+            dead2[c] = d ? 1 : 0;
+            thr2[c] = d ? 0ull : (((unsigned long long)(uint32_t)score[n] << 32) | (uint32_t)pair[n]);
+        }
+    }
+}
+
 __global__ void k_coarse_src(int32_t E, const int32_t *src, const uint8_t *sdst,
                              const int32_t *gamma, const int32_t *noff2, const int32_t *inn2,
                              int32_t *src2, uint8_t *sdst2) {
@@ -147,7 +165,8 @@ static int grid1d(int64_t n) {
 // Builds level `H` (V2 nodes) from level `L` and its match/gamma.  Device
 // allocations of H go to `keep`; temporaries to `tmp`.
 cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
-                         int32_t *status, cudaStream_t s) {
+                         const int32_t *pair, const int32_t *score, int32_t *status,
+                         cudaStream_t s) {
     cudaError_t e;
     H.V = V2;
     H.E = L.E;
@@ -164,9 +183,18 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (!e) e = dalloc(keep, &H.poff, (size_t)L.E + 1);
     if (!e) e = dalloc(keep, &H.src, L.E);
     if (!e) e = dalloc(keep, &H.sdst, L.E);
+    if (!e) e = dalloc(keep, &H.dead, V2);
+    if (!e) e = dalloc(keep, &H.merged, V2);
+    if (!e) e = dalloc(keep, &H.thr, V2);
+    if (!e) e = dalloc(keep, &H.old_id, V2);
     if (e) return e;
     k_coarse_nodes<<<grid1d(L.V), 256, 0, s>>>(L.V, L.match, L.gamma, L.w, rep_of, H.w);
     count_launch();
+    k_carry<<<grid1d(L.V), 256, 0, s>>>(L.V, pair, score, L.match, L.gamma, L.dead, H.dead,
+                                        H.merged, H.thr);
+    count_launch();
+    e = cudaMemcpyAsync(H.old_id, rep_of, sizeof(int32_t) * (size_t)V2, cudaMemcpyDeviceToDevice, s);
+    if (e) return e;
     k_union<false><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
                                                   L.inn, cntI, cntN, nullptr, nullptr, nullptr,
                                                   nullptr, dmax);

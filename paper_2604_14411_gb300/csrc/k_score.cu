@@ -43,7 +43,20 @@ struct ScoreArgs {
     unsigned long long *bytes;
     const uint32_t *bm;              // bitmap mode: [V][bm_words] rows of in()
     int32_t bm_words;                // multiple of 4 (16-byte rows); 0 = list mode
+    const uint8_t *dead, *merged;    // carried level state (null at level 0)
+    const unsigned long long *thr;
+    const int32_t *old_id;
 };
+
+// m is worth checking for n: alive, and either newly merged or ranked below
+// n's previous candidate (the ones above it were already invalid).
+__device__ __forceinline__ bool eligible(const ScoreArgs &a, int32_t m, int32_t h,
+                                         unsigned long long thr) {
+    if (a.dead && a.dead[m]) return false;
+    if (thr == 0ull || a.merged[m]) return true;
+    unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)a.old_id[m];
+    return key < thr;
+}
 
 __device__ __forceinline__ uint32_t hash_u32(uint32_t x) {
     x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
@@ -117,6 +130,11 @@ k_score(ScoreArgs a) {
     unsigned long long bytes = 0;
 
     for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
+        if (a.dead && a.dead[n]) {              // no valid candidate can exist
+            if (threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; }
+            continue;
+        }
+        const unsigned long long thr = a.thr ? a.thr[n] : 0ull;
         // ---- clear; stage row(n) ----
         for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
             if (DENSE) hist[i] = 0;
@@ -161,7 +179,7 @@ k_score(ScoreArgs a) {
             int32_t hm = 0;
             for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
                 int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
-                if (h < hcur && h > hm) hm = h;
+                if (h < hcur && h > hm && eligible(a, DENSE ? i : gkeys[i], h, thr)) hm = h;
             }
             int32_t hmax = block_max_i32(hm, red);
             if (hmax == 0) break;
@@ -173,7 +191,7 @@ k_score(ScoreArgs a) {
                 // ids are table indices: scan downwards, the first valid is this warp's best
                 for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
                     int32_t i = base + lane_id();
-                    bool hit = i < hi && hist[i] == hmax;
+                    bool hit = i < hi && hist[i] == hmax && eligible(a, i, hmax, thr);
                     unsigned ball = __ballot_sync(0xffffffffu, hit);
                     while (ball && best_id < 0) {
                         int src = 31 - __clz(ball);
@@ -185,7 +203,8 @@ k_score(ScoreArgs a) {
                 for (int32_t base = lo; base < hi; base += 32) {
                     int32_t i = base + lane_id();
                     int32_t m = -1;
-                    if (i < hi && gkeys[i] >= 0 && gvals[i] == hmax) m = gkeys[i];
+                    if (i < hi && gkeys[i] >= 0 && gvals[i] == hmax && eligible(a, gkeys[i], hmax, thr))
+                        m = gkeys[i];
                     unsigned ball = __ballot_sync(0xffffffffu, m >= 0);
                     while (ball) {
                         int src = __ffs(ball) - 1;
@@ -260,6 +279,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     a.noff = L.noff; a.inn = L.inn; a.ew = ew;
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score; a.status = status; a.bytes = bytes;
+    a.dead = L.dead; a.merged = L.merged; a.thr = L.thr; a.old_id = L.old_id;
     cudaError_t e;
     // bitmaps only when some pair may need a union count
     int32_t words = ((L.E + 31) / 32 + 3) & ~3;
