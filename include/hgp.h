@@ -46,7 +46,8 @@ typedef enum {
     HGP_ERR_OOM = 3,           /* device allocation failed */
     HGP_ERR_CUDA = 4,          /* a CUDA call failed (message has the detail) */
     HGP_ERR_DEVICE_LIMIT = 5,  /* a bounded device loop ran out of its budget */
-    HGP_ERR_STATE = 6          /* call not valid in the handle's current state */
+    HGP_ERR_STATE = 6,         /* call not valid in the handle's current state */
+    HGP_ERR_SCRATCH_LIMIT = 7  /* input too large for hgp_score_noalloc's fixed scratch */
 } hgp_status;
 
 /* hgp_create flags */
@@ -171,6 +172,48 @@ const char *hgp_last_error(const hgp_graph *g);
 
 /* Frees the handle and all device memory it owns (after syncing its stream). */
 void hgp_destroy(hgp_graph *g);
+
+/*
+ * hgp_score_noalloc -- candidate scoring of one level without any device
+ * allocation.  (The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory while they run -- code inside another
+ * framework's memory pool or allocator callback, runtimes that reserved all
+ * device memory up front, or steps that must not incur the implicit
+ * synchronisation of cudaMalloc/cudaFree.)
+ *
+ * Computes, for every node n, the same pair(n) and score(n) that
+ * hgp_partition computes at its first level (HGP_LEVEL_PAIR / HGP_LEVEL_SCORE
+ * of level 0): the first neighbour m in (hist desc, id desc) order with
+ * w(n) + w(m) <= omega and |in(n) u in(m)| <= delta, -1 and 0 if none.
+ * All pointers are device memory, readable/writable on `stream`:
+ *   offsets[E+1], pins[P]          pins of every hyperedge
+ *   inc_offsets[N+1], inc[P]       I(n), the hyperedges containing n
+ *   in_offsets[N+1], in_edges[Q]   in(n), ascending edge ids
+ *   node_weights[N], edge_weights[E] (both required, >= 1)
+ *   pair[N], score[N]              outputs
+ * Inputs are not validated beyond null pointers and sizes; they must satisfy
+ * the rules of hgp_create.
+ * Scratch: one library-owned 16 MiB device array per GPU (allocated when the
+ * library is loaded, held until the process exits).  The in() bitmaps need
+ * N * 4 * ceil(E / 128) * 16 bytes whenever 2 * max |in(n)| > delta; larger
+ * inputs, or N too large for the shared-memory histogram (about 54,000
+ * nodes), return HGP_ERR_SCRATCH_LIMIT without launching anything.  The call
+ * clears the part of the array it uses, so the previous call's contents do not
+ * matter; but every call on a device shares the array, so calls whose work
+ * overlaps on the GPU (e.g. on two streams) race -- serialise them.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  The call synchronises `stream` once (to read
+ * the largest |in(n)|).  Returns HGP_OK, HGP_ERR_INVALID_ARG,
+ * HGP_ERR_SCRATCH_LIMIT or HGP_ERR_CUDA.
+ */
+int hgp_score_noalloc(int32_t num_nodes, int32_t num_edges,
+                      const int32_t *offsets, const int32_t *pins,
+                      const int32_t *inc_offsets, const int32_t *inc,
+                      const int32_t *in_offsets, const int32_t *in_edges,
+                      const int32_t *node_weights, const int32_t *edge_weights,
+                      int64_t omega, int64_t delta,
+                      int32_t *pair, int32_t *score, void *stream);
 
 #ifdef __cplusplus
 }

@@ -494,6 +494,7 @@ extern "C" const char *hgp_error_string(int status) {
     case HGP_ERR_CUDA: return "CUDA error";
     case HGP_ERR_DEVICE_LIMIT: return "device loop budget exhausted";
     case HGP_ERR_STATE: return "invalid handle state";
+    case HGP_ERR_SCRATCH_LIMIT: return "input exceeds the fixed scratch of hgp_score_noalloc";
     default: return "unknown status";
     }
 }

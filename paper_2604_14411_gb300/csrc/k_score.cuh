@@ -1,0 +1,266 @@
+// Candidate scoring (Sec. III-A, Eq. (2)) fused with the deferred validity
+// checks of Sec. III-B.2.
+//
+// One CTA per node n (persistent grid, nodes strided over CTAs).
+//   1. hist(n, m) = sum of omega(e) over e in I(n), m in e, m != n.
+//      Each warp takes hyperedges of I(n); its lanes read the pins of one
+//      hyperedge with coalesced int32 loads and add omega(e) into the
+//      histogram:
+//        dense mode  -- a |N_l|-entry int32 array in shared memory,
+//                       indexed by node id (one smem atomic per pin visit);
+//        hash mode   -- a per-CTA open-addressing table in global memory
+//                       (levels whose node count does not fit on chip).
+//   2. Candidates are extracted by decreasing hist value.  For the current
+//      top value h, every neighbour with hist = h is checked in parallel
+//      (one warp per candidate); the valid one of largest id wins.  If none
+//      is valid the next lower value is taken.  This visits candidates in
+//      the paper's (hist desc, id desc) order and returns the first valid
+//      one, checking a whole tie group at once.
+//   3. Check of a pair (n, m): w(n) + w(m) <= Omega, and
+//      |in(n) u in(m)| <= Delta.  When |in(n)| + |in(m)| <= Delta the pair is
+//      valid without counting.  Otherwise the union is counted either
+//        bitmap mode -- as popcount(row(n) | row(m)) over per-node bitmaps of
+//                       in() with one bit per hyperedge (row(n) staged in
+//                       shared memory, row(m) read with 16-byte loads), or
+//        list mode   -- as |in(n)| + |in(m) \ in(n)| with a binary search in
+//                       the sorted in(n), stopping as soon as Delta is
+//                       exceeded (levels whose bitmaps would not fit).
+#pragma once
+#include "hgp_internal.cuh"
+
+namespace hgp {
+
+constexpr int kScoreThreads = 512;
+constexpr int kScoreWarps = kScoreThreads / 32;
+
+struct ScoreArgs {
+    int32_t V, E;
+    const int32_t *w, *poff, *pins, *ioff, *inc, *noff, *inn, *ew;
+    int64_t omega, delta;
+    int32_t *pair, *score;
+    int32_t *status;
+    int32_t *gkeys, *gvals;          // hash mode: per-CTA tables of gcap entries
+    int32_t gcap;
+    unsigned long long *bytes;
+    const uint32_t *bm;              // bitmap mode: [V][bm_words] rows of in()
+    int32_t bm_words;                // multiple of 4 (16-byte rows); 0 = list mode
+    const uint8_t *dead, *merged;    // carried level state (null at level 0)
+    const unsigned long long *thr;
+    const int32_t *old_id;
+};
+
+// m is worth checking for n: alive, and either newly merged or ranked below
+// n's previous candidate (the ones above it were already invalid).
+__device__ __forceinline__ bool eligible(const ScoreArgs &a, int32_t m, int32_t h,
+                                         unsigned long long thr) {
+    if (a.dead && a.dead[m]) return false;
+    if (thr == 0ull || a.merged[m]) return true;
+    unsigned long long key = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)a.old_id[m];
+    return key < thr;
+}
+
+__device__ __forceinline__ uint32_t hash_u32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane_id() == 0) red[warp_id()] = v;
+    __syncthreads();
+    int32_t r = red[0];
+#pragma unroll
+    for (int i = 1; i < kScoreWarps; ++i) r = max(r, red[i]);
+    return r;
+}
+
+// Warp-cooperative validity test of pair (n, m); all lanes return the same.
+static __device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, const uint32_t *row_n,
+                           int64_t in_n, unsigned long long &bytes) {
+    if ((int64_t)a.w[n] + a.w[m] > a.omega) return false;
+    int32_t m0 = a.noff[m], m1 = a.noff[m + 1];
+    int64_t in_m = m1 - m0;
+    if (in_n + in_m <= a.delta) return true;
+    if (a.bm_words) {
+        const uint4 *rm = reinterpret_cast<const uint4 *>(a.bm + (int64_t)m * a.bm_words);
+        const uint4 *rn = reinterpret_cast<const uint4 *>(row_n);
+        int32_t q = a.bm_words >> 2;
+        int32_t u = 0;
+        for (int32_t i = lane_id(); i < q; i += 32) {
+            uint4 x = rm[i], y = rn[i];
+            u += __popc(x.x | y.x) + __popc(x.y | y.y) + __popc(x.z | y.z) + __popc(x.w | y.w);
+        }
+        u = warp_sum(u);
+        if (lane_id() == 0) bytes += 4ull * (unsigned long long)a.bm_words;
+        return u <= a.delta;
+    }
+    int32_t n0 = a.noff[n], n1 = a.noff[n + 1];
+    int64_t room = a.delta - in_n;          // edges of in(m) allowed outside in(n)
+    int64_t extra = 0;
+    int32_t seen = 0;
+    for (int32_t base = m0; base < m1; base += 128) {
+        int32_t miss = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int32_t j = base + u * 32 + lane_id();
+            if (j < m1) miss += contains_sorted(a.inn, n0, n1, a.inn[j]) ? 0 : 1;
+        }
+        extra += warp_sum(miss);
+        seen += min(128, m1 - base);
+        if (extra > room) break;
+    }
+    if (lane_id() == 0) bytes += 4ull * (unsigned long long)seen;
+    return extra <= room;
+}
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kScoreThreads)
+k_score(ScoreArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    // layout: [row of in(n): bm_words][dense hist V]
+    uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
+    int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
+    __shared__ int32_t red[kScoreWarps];
+
+    int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
+    int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
+    const int32_t cap = DENSE ? a.V : a.gcap;
+    const uint32_t mask = (uint32_t)a.gcap - 1u;
+    unsigned long long bytes = 0;
+
+    for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
+        if (a.dead && a.dead[n]) {              // no valid candidate can exist
+            if (threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; }
+            continue;
+        }
+        const unsigned long long thr = a.thr ? a.thr[n] : 0ull;
+        // ---- clear; stage row(n) ----
+        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+            if (DENSE) hist[i] = 0;
+            else { gkeys[i] = -1; gvals[i] = 0; }
+        }
+        if (a.bm_words) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.bm + (int64_t)n * a.bm_words);
+            uint4 *dst = reinterpret_cast<uint4 *>(row_n);
+            for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+        // ---- Eq. (2) accumulation ----
+        int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
+        for (int32_t k = i0 + warp_id(); k < i1; k += kScoreWarps) {
+            int32_t e = a.inc[k];
+            int32_t we = a.ew[e];
+            int32_t p0 = a.poff[e], p1 = a.poff[e + 1];
+            for (int32_t j = p0 + lane_id(); j < p1; j += 32) {
+                int32_t m = a.pins[j];
+                if (m == n) continue;
+                if (DENSE) {
+                    atomicAdd(&hist[m], we);
+                } else {
+                    uint32_t slot = hash_u32((uint32_t)m) & mask;
+                    int32_t probes = 0;
+                    for (;;) {
+                        int32_t k0 = atomicCAS(&gkeys[slot], -1, m);
+                        if (k0 == -1 || k0 == m) { atomicAdd(&gvals[slot], we); break; }
+                        slot = (slot + 1) & mask;
+                        if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
+                    }
+                }
+            }
+            if (lane_id() == 0)
+                bytes += 16ull + 4ull * (unsigned long long)(p1 - p0);  // inc, omega, 2 offsets, pins
+        }
+        __syncthreads();
+        // ---- extraction by decreasing hist value ----
+        int64_t in_n = a.noff[n + 1] - a.noff[n];
+        int32_t hcur = 0x7fffffff, result = -1, rscore = 0;
+        for (;;) {
+            int32_t hm = 0;
+            for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+                int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
+                if (h < hcur && h > hm && eligible(a, DENSE ? i : gkeys[i], h, thr)) hm = h;
+            }
+            int32_t hmax = block_max_i32(hm, red);
+            if (hmax == 0) break;
+            // every neighbour with hist == hmax, one warp per candidate
+            int32_t best_id = -1;
+            int32_t per_warp = (((cap + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+            int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
+            if (DENSE) {
+                // ids are table indices: scan downwards, the first valid is this warp's best
+                for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
+                    int32_t i = base + lane_id();
+                    bool hit = i < hi && hist[i] == hmax && eligible(a, i, hmax, thr);
+                    unsigned ball = __ballot_sync(0xffffffffu, hit);
+                    while (ball && best_id < 0) {
+                        int src = 31 - __clz(ball);
+                        ball &= ~(1u << src);
+                        if (warp_check(a, n, base + src, row_n, in_n, bytes)) best_id = base + src;
+                    }
+                }
+            } else {
+                for (int32_t base = lo; base < hi; base += 32) {
+                    int32_t i = base + lane_id();
+                    int32_t m = -1;
+                    if (i < hi && gkeys[i] >= 0 && gvals[i] == hmax && eligible(a, gkeys[i], hmax, thr))
+                        m = gkeys[i];
+                    unsigned ball = __ballot_sync(0xffffffffu, m >= 0);
+                    while (ball) {
+                        int src = __ffs(ball) - 1;
+                        ball &= ball - 1;
+                        int32_t cm = __shfl_sync(0xffffffffu, m, src);
+                        if (cm > best_id && warp_check(a, n, cm, row_n, in_n, bytes)) best_id = cm;
+                    }
+                }
+            }
+            int32_t win = block_max_i32(best_id, red);
+            if (win >= 0) { result = win; rscore = hmax; break; }
+            hcur = hmax;
+        }
+        if (threadIdx.x == 0) {
+            a.pair[n] = result;
+            a.score[n] = result >= 0 ? rscore : 0;
+            bytes += 8ull + 8ull;   // I(n) offsets, pair/score writes
+        }
+        __syncthreads();
+    }
+    if (a.bytes) {
+        bytes = warp_sum(bytes);
+        if (lane_id() == 0 && bytes) atomicAdd(a.bytes, bytes);
+    }
+}
+
+// Largest per-node pin-visit count sum_{e in I(n)} |e| (bounds the distinct
+// neighbours and sizes the hash tables).
+static __global__ void k_max_work(int32_t V, const int32_t *ioff, const int32_t *inc, const int32_t *poff,
+                           unsigned long long *out) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        unsigned long long s = 0;
+        for (int32_t k = ioff[n] + lane_id(); k < ioff[n + 1]; k += 32) {
+            int32_t e = inc[k];
+            s += (unsigned long long)(poff[e + 1] - poff[e]);
+        }
+        s = warp_sum(s);
+        if (lane_id() == 0) atomicMax(out, s);
+    }
+}
+
+// Rows of in(): bit e of row n is set iff e in in(n).
+static __global__ void k_in_bitmap(int32_t V, const int32_t *noff, const int32_t *inn, int32_t words,
+                            uint32_t *bm) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        uint32_t *row = bm + n * words;
+        for (int32_t j = noff[n] + lane_id(); j < noff[n + 1]; j += 32) {
+            int32_t e = inn[j];
+            atomicOr(&row[e >> 5], 1u << (e & 31));
+        }
+    }
+}
+
+}  // namespace hgp

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhgp.so")
 
 HGP_OK, HGP_ERR_INVALID_ARG, HGP_ERR_INFEASIBLE, HGP_ERR_OOM = 0, 1, 2, 3
-HGP_ERR_CUDA, HGP_ERR_DEVICE_LIMIT, HGP_ERR_STATE = 4, 5, 6
+HGP_ERR_CUDA, HGP_ERR_DEVICE_LIMIT, HGP_ERR_STATE, HGP_ERR_SCRATCH_LIMIT = 4, 5, 6, 7
 HGP_INPUT_DEVICE = 1
 HGP_OUTPUT_DEVICE = 1
 HGP_DEBUG_KEEP_LEVELS = 1
@@ -66,7 +66,8 @@ class hgp_stats(ctypes.Structure):
 
 # every symbol declared in include/hgp.h
 EXPORTS = ("hgp_create", "hgp_partition", "hgp_get_stats", "hgp_get_level_len",
-           "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy")
+           "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy",
+           "hgp_score_noalloc")
 
 _lib = None
 
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.hgp_last_error.restype = ctypes.c_char_p
     lib.hgp_destroy.argtypes = [vp]
     lib.hgp_destroy.restype = None
+    lib.hgp_score_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i64, i64, vp, vp, vp]
+    lib.hgp_score_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
