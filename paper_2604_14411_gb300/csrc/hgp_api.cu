@@ -20,13 +20,9 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
                          cudaStream_t s);
 int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
                      cudaError_t *cerr, std::string *why, cudaStream_t s);
-struct RefineOut {
-    int32_t M, kstar;
-    long long gain;
-};
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
-                            int32_t K, int64_t omega, int64_t delta, RefineOut *out,
-                            uint32_t debug, cudaStream_t s);
+                            int32_t K, int64_t omega, int64_t delta, long long *d_stats,
+                            unsigned long long *d_applied, uint32_t debug, cudaStream_t s);
 void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
                  cudaStream_t s);
 cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
@@ -272,6 +268,8 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     Arena lv, tmp;
     lv.stream = s;
     tmp.stream = s;
+    lv.min_chunk = (size_t)64 << 20;
+    tmp.min_chunk = (size_t)64 << 20;
     Timer tm;
     tm.on = (debug & HGP_DEBUG_TIMING) != 0;
     tm.s = s;
@@ -357,8 +355,7 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
             tm.stop(2, ev_a);
             levels.push_back(H);
             pins_total += H.P;
-            CKP(cudaStreamSynchronize(s), "sync");
-            tmp.release_all();
+            tmp.reset();               // stream order keeps the reuse safe
         }
     }
     double c1 = now_ms();
@@ -372,24 +369,29 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
                             cudaMemcpyDeviceToDevice, s), "copy gamma");
     else
         iota_i32(rho, levels[L].V, s);
-    int64_t moves_applied = 0;
-    std::vector<int64_t> rstat;
+    long long *d_rstat = nullptr;
+    unsigned long long *d_applied = nullptr;
+    CKP(dalloc(lv, &d_rstat, 3 * levels.size()), "alloc");
+    CKP(dalloc(lv, &d_applied, 1), "alloc");
+    CKP(cudaMemsetAsync(d_rstat, 0, sizeof(long long) * 3 * levels.size(), s), "memset");
+    CKP(cudaMemsetAsync(d_applied, 0, sizeof(unsigned long long), s), "memset");
     tm.start(3, &ev_a);
     for (int l = L; l >= 0; --l) {
         const Level &Lv = levels[l];
         if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
-        RefineOut ro{0, 0, 0};
         for (int p = 0; p < passes; ++p) {
-            CKP(run_refine_pass(tmp, Lv, g->ew, rho, K, omega, delta, &ro, debug, s), "refine");
-            CKP(cudaStreamSynchronize(s), "sync");
-            moves_applied += ro.kstar;
-            tmp.release_all();
+            CKP(run_refine_pass(tmp, Lv, g->ew, rho, K, omega, delta, d_rstat + 3 * l, d_applied,
+                                debug, s), "refine");
+            tmp.reset();
         }
         if (debug & HGP_DEBUG_KEEP_LEVELS) {
             keep_array(g, HGP_LEVEL_RHO_OUT, l, rho, Lv.V, s);
+            long long st3[3];
+            CKP(cudaMemcpyAsync(st3, d_rstat + 3 * l, sizeof(st3), cudaMemcpyDeviceToHost, s), "stats");
+            CKP(cudaStreamSynchronize(s), "sync");
             auto &vv = g->dbg[HGP_LEVEL_REFINE];
             if ((int)vv.size() <= l) vv.resize(l + 1);
-            vv[l] = {ro.M, ro.kstar, ro.gain};
+            vv[l] = {st3[0], st3[1], st3[2]};
         }
         if (l > 0) {
             int32_t *rf = nullptr;
@@ -415,8 +417,9 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     CKP(dalloc(tmp, &d_cost, 1), "alloc");
     CKP(dalloc(tmp, &d_np, 1), "alloc");
     CKP(run_finalize(tmp, g->L0, g->ew, rho, K, d_ids, d_pw, d_pin, d_cost, d_np, s), "finalize");
-    unsigned long long cost = 0;
+    unsigned long long cost = 0, applied = 0;
     int32_t np = 0;
+    CKP(cudaMemcpyAsync(&applied, d_applied, sizeof(applied), cudaMemcpyDeviceToHost, s), "read stats");
     CKP(cudaMemcpyAsync(&cost, d_cost, sizeof(cost), cudaMemcpyDeviceToHost, s), "read cost");
     CKP(cudaMemcpyAsync(&np, d_np, sizeof(np), cudaMemcpyDeviceToHost, s), "read parts");
     if (!outdev) {
@@ -444,7 +447,7 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     st.num_parts = np;
     st.cost = res->cost;
     st.pins_total = pins_total;
-    st.moves_applied = moves_applied;
+    st.moves_applied = (int64_t)applied;
     if (tm.on) {
         st.ms_score = tm.total(0);
         st.ms_match = tm.total(1);

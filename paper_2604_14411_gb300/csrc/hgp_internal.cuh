@@ -52,10 +52,18 @@ struct Level {
 };
 
 // ---------------- stream-ordered device memory ----------------
+// Bump allocator over device chunks obtained with cudaMallocAsync on
+// `stream`.  reset() makes every allocation dead and reuses the chunks from
+// the start; this is safe because all work runs in order on the one stream.
+// With min_chunk = 0 every allocation gets an exact chunk of its own.
 struct Arena {
+    struct Chunk { char *base; size_t size; };
     cudaStream_t stream = nullptr;
-    std::vector<void *> live;
+    size_t min_chunk = 0;
+    std::vector<Chunk> chunks;
+    size_t cur = 0, off = 0;
     cudaError_t alloc(void **p, size_t bytes);
+    void reset() { cur = 0; off = 0; }
     void release_all();
 };
 

@@ -61,27 +61,44 @@ __device__ int32_t warp_union(const int32_t *A, int32_t na, const int32_t *B, in
     return na + nb - dupA;
 }
 
-template <bool WRITE>
-__global__ void k_union(int32_t V2, const int32_t *rep_of, const int32_t *match,
-                        const int32_t *ioff, const int32_t *inc, const int32_t *noff,
-                        const int32_t *inn, int32_t *cntI, int32_t *cntN,
-                        const int32_t *ioff2, int32_t *inc2, const int32_t *noff2,
-                        int32_t *inn2, int32_t *max_in) {
+// Count pass: a warp per coarse node; unmatched nodes keep their lists.
+__global__ void k_union_count(int32_t V2, const int32_t *rep_of, const int32_t *match,
+                              const int32_t *ioff, const int32_t *inc, const int32_t *noff,
+                              const int32_t *inn, int32_t *cntI, int32_t *cntN, int32_t *max_in) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = gw; c < V2; c += nw) {
         int32_t a = rep_of[c], b = match[a];
-        const int32_t *Ia = inc + ioff[a], *Na = inn + noff[a];
         int32_t nIa = ioff[a + 1] - ioff[a], nNa = noff[a + 1] - noff[a];
-        const int32_t *Ib = Ia, *Nb = Na;
-        int32_t nIb = 0, nNb = 0;
+        int32_t ci = nIa, cn = nNa;
         if (b != a) {
-            Ib = inc + ioff[b]; nIb = ioff[b + 1] - ioff[b];
-            Nb = inn + noff[b]; nNb = noff[b + 1] - noff[b];
+            ci = warp_union<false>(inc + ioff[a], nIa, inc + ioff[b], ioff[b + 1] - ioff[b], nullptr);
+            cn = warp_union<false>(inn + noff[a], nNa, inn + noff[b], noff[b + 1] - noff[b], nullptr);
         }
-        int32_t ci = warp_union<WRITE>(Ia, nIa, Ib, nIb, WRITE ? inc2 + ioff2[c] : nullptr);
-        int32_t cn = warp_union<WRITE>(Na, nNa, Nb, nNb, WRITE ? inn2 + noff2[c] : nullptr);
-        if (!WRITE && lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; atomicMax(max_in, cn); }
+        if (lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; atomicMax(max_in, cn); }
+    }
+}
+
+// Write pass: a CTA per coarse node; unmatched nodes are copied by the whole
+// CTA, matched pairs are merged by its first warp.
+__global__ void k_union_write(int32_t V2, const int32_t *rep_of, const int32_t *match,
+                              const int32_t *ioff, const int32_t *inc, const int32_t *noff,
+                              const int32_t *inn, const int32_t *ioff2, int32_t *inc2,
+                              const int32_t *noff2, int32_t *inn2) {
+    for (int32_t c = blockIdx.x; c < V2; c += gridDim.x) {
+        int32_t a = rep_of[c], b = match[a];
+        if (b == a) {
+            int32_t i0 = ioff[a], n0 = noff[a];
+            int32_t ni = ioff[a + 1] - i0, nn = noff[a + 1] - n0;
+            int32_t *oi = inc2 + ioff2[c], *on = inn2 + noff2[c];
+            for (int32_t t = threadIdx.x; t < ni; t += blockDim.x) oi[t] = inc[i0 + t];
+            for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) on[t] = inn[n0 + t];
+        } else if (threadIdx.x < 32) {
+            warp_union<true>(inc + ioff[a], ioff[a + 1] - ioff[a], inc + ioff[b], ioff[b + 1] - ioff[b],
+                             inc2 + ioff2[c]);
+            warp_union<true>(inn + noff[a], noff[a + 1] - noff[a], inn + noff[b], noff[b + 1] - noff[b],
+                             inn2 + noff2[c]);
+        }
     }
 }
 
@@ -195,9 +212,8 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     count_launch();
     e = cudaMemcpyAsync(H.old_id, rep_of, sizeof(int32_t) * (size_t)V2, cudaMemcpyDeviceToDevice, s);
     if (e) return e;
-    k_union<false><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
-                                                  L.inn, cntI, cntN, nullptr, nullptr, nullptr,
-                                                  nullptr, dmax);
+    k_union_count<<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
+                                                 L.inn, cntI, cntN, dmax);
     count_launch();
     k_coarse_pins<false><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
                                                          L.ioff, L.inc, cntP, nullptr, nullptr);
@@ -221,9 +237,11 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (!e) e = dalloc(keep, &H.inn, H.Q);
     if (!e) e = dalloc(keep, &H.pins, H.P);
     if (e) return e;
-    k_union<true><<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
-                                                 L.inn, nullptr, nullptr, H.ioff, H.inc, H.noff,
-                                                 H.inn, nullptr);
+    {
+        int blocks = V2 < num_sms() * 16 ? V2 : num_sms() * 16;
+        k_union_write<<<blocks, 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff, L.inn,
+                                             H.ioff, H.inc, H.noff, H.inn);
+    }
     count_launch();
     k_coarse_pins<true><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
                                                         L.ioff, L.inc, nullptr, H.poff, H.pins);

@@ -20,14 +20,31 @@ int num_sms() {
 }
 
 cudaError_t Arena::alloc(void **p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, bytes, stream);
-    if (e == cudaSuccess) live.push_back(*p);
-    return e;
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (cur < chunks.size()) {
+        if (off + bytes <= chunks[cur].size) {
+            *p = chunks[cur].base + off;
+            off += bytes;
+            return cudaSuccess;
+        }
+        ++cur;
+        off = 0;
+    }
+    size_t sz = bytes > min_chunk ? bytes : min_chunk;
+    void *b = nullptr;
+    cudaError_t e = cudaMallocAsync(&b, sz, stream);
+    if (e != cudaSuccess) return e;
+    chunks.push_back({static_cast<char *>(b), sz});
+    cur = chunks.size() - 1;
+    off = bytes;
+    *p = b;
+    return cudaSuccess;
 }
 
 void Arena::release_all() {
-    for (void *p : live) cudaFreeAsync(p, stream);
-    live.clear();
+    for (auto &c : chunks) cudaFreeAsync(c.base, stream);
+    chunks.clear();
+    cur = off = 0;
 }
 
 // ---------------------------------------------------------------- scans

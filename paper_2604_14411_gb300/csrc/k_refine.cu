@@ -306,21 +306,32 @@ __global__ void k_gather_u32(int64_t n, const int32_t *src, const int32_t *idx, 
         out[i] = (uint32_t)src[idx[i]];
 }
 
-// after the sorts: part of each event and the +-1 deltas (events at even ids
-// leave, at odd ids enter)
-__global__ void k_seq_prep(int64_t nev, const int32_t *jS, const uint32_t *ev_p,
-                           const uint8_t *ev_dst, int32_t *pS, int32_t *d_all, int32_t *d_in) {
+// after the sorts: part of each event, the +-1 deltas (events at even ids
+// leave, at odd ids enter) and the first-of-(e, p)-group flags
+__global__ void k_seq_prep(int64_t nev, const uint32_t *eS, const int32_t *jS, const uint32_t *ev_p,
+                           const uint8_t *ev_dst, int32_t *pS, int32_t *d_all, int32_t *d_in,
+                           int32_t *head) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t j = jS[i];
         int32_t d = (j & 1) ? 1 : -1;
-        pS[i] = (int32_t)ev_p[j];
+        int32_t p = (int32_t)ev_p[j];
+        pS[i] = p;
         d_all[i] = d;
         d_in[i] = ev_dst[j] ? d : 0;
+        head[i] = (i == 0 || eS[i - 1] != eS[i] || (int32_t)ev_p[jS[i - 1]] != p) ? 1 : 0;
     }
 }
 
+// position of the first event of every group (gidx = exclusive count of heads)
+__global__ void k_group_starts(int64_t nev, const int32_t *head, const int32_t *gidx, int32_t *gstart) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (head[i]) gstart[gidx[i]] = (int32_t)i;
+}
+
 __global__ void k_seq_apply(int64_t nev, const uint32_t *eS, const int32_t *pS, const int32_t *jS,
+                            const int32_t *head, const int32_t *gidx, const int32_t *gstart,
                             const int32_t *pre_all, const int32_t *pre_in, const int32_t *ev_k,
                             const uint8_t *ev_dst, const int32_t *poff, const int32_t *nrun,
                             const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
@@ -330,12 +341,7 @@ __global__ void k_seq_apply(int64_t nev, const uint32_t *eS, const int32_t *pS, 
         uint32_t e = eS[i];
         int32_t p = pS[i];
         // first event of the same (e, p) group
-        int64_t lo = 0, hi = i;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            bool less = eS[mid] < e || (eS[mid] == e && pS[mid] < p);
-            if (less) lo = mid + 1; else hi = mid;
-        }
+        int64_t lo = gstart[gidx[i] + head[i] - 1];
         int32_t r0 = poff[e], r1 = r0 + nrun[e];
         int32_t q = lower_bound_i32(rpart, r0, r1, p);
         int32_t c0 = 0, c0in = 0;
@@ -422,9 +428,10 @@ __global__ void k_gseq_i64(int32_t M, const int32_t *gseq, const int32_t *vdelta
     }
 }
 
-// single CTA: k* = argmax over valid prefixes of (G, length); apply iff G > 0
+// single CTA: k* = argmax over valid prefixes of (G, length); apply iff G > 0.
+// stats[0..2] = (M, k*, gain); *applied accumulates k* over passes.
 __global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32_t *kstar,
-                         long long *gain) {
+                         long long *stats, unsigned long long *applied) {
     __shared__ long long bg[1024];
     __shared__ int32_t bk[1024];
     long long g = 0;
@@ -452,7 +459,8 @@ __global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32
     if (threadIdx.x == 0) {
         bool apply = bk[0] != 0 && bg[0] > 0;
         *kstar = apply ? bk[0] : 0;
-        *gain = apply ? bg[0] : 0;
+        if (stats) { stats[0] = M; stats[1] = apply ? bk[0] : 0; stats[2] = apply ? bg[0] : 0; }
+        if (applied && apply) atomicAdd(applied, (unsigned long long)bk[0]);
     }
 }
 
@@ -484,16 +492,11 @@ __global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
         flag[n] = gain[n] > 0 ? 1 : 0;
 }
 
-struct RefineOut {
-    int32_t M, kstar;
-    long long gain;
-};
-
 // One refinement pass on level L; rho is updated in place on the device.
+// d_stats (device, 3 x int64) receives (M, k*, gain); *d_applied adds k*.
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
-                            int32_t K, int64_t omega, int64_t delta, RefineOut *out,
-                            uint32_t debug, cudaStream_t s) {
-    out->M = 0; out->kstar = 0; out->gain = 0;
+                            int32_t K, int64_t omega, int64_t delta, long long *d_stats,
+                            unsigned long long *d_applied, uint32_t debug, cudaStream_t s) {
     int32_t V = L.V;
     int32_t *size, *inb;
     cudaError_t e = dalloc(tmp, &size, K);
@@ -548,8 +551,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     e = cudaMemcpyAsync(&M, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return e;
-    out->M = M;
-    if (M == 0) return cudaSuccess;
+    if (M == 0) return cudaMemsetAsync(d_stats, 0, 3 * sizeof(long long), s);
     uint32_t *mkey, *mkey2;
     int32_t *mnode, *mv_n, *mv_ps, *mv_pd, *idx_of, *gseq, *lose, *gin;
     e = dalloc(tmp, &mkey, M);
@@ -615,15 +617,24 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
         count_launch();
         e = radix_sort_pairs(tmp, e1, j1, eS, jS, nq, bits_for(L.E > 0 ? L.E - 1 : 0), s);
         if (e) return e;
-        k_seq_prep<<<grid1d(nq), 256, 0, s>>>(nq, jS, ev_p, ev_dst, pS, d_all, d_in);
+        int32_t *head, *gidx, *gstart;
+        e = dalloc(tmp, &head, nq);
+        if (!e) e = dalloc(tmp, &gidx, nq);
+        if (!e) e = dalloc(tmp, &gstart, nq);
+        if (e) return e;
+        k_seq_prep<<<grid1d(nq), 256, 0, s>>>(nq, eS, jS, ev_p, ev_dst, pS, d_all, d_in, head);
         count_launch();
         e = exclusive_scan_i32(tmp, d_all, pre_all, nq, nullptr, s);
         if (!e) e = exclusive_scan_i32(tmp, d_in, pre_in, nq, nullptr, s);
+        if (!e) e = exclusive_scan_i32(tmp, head, gidx, nq, nullptr, s);
         if (e) return e;
+        k_group_starts<<<grid1d(nq), 256, 0, s>>>(nq, head, gidx, gstart);
+        count_launch();
         cudaMemsetAsync(gseq, 0, sizeof(int32_t) * (size_t)M, s);
         cudaMemsetAsync(lose, 0, sizeof(int32_t) * (size_t)M, s);
         cudaMemsetAsync(gin, 0, sizeof(int32_t) * (size_t)M, s);
-        k_seq_apply<<<grid1d(nq), 256, 0, s>>>(nq, eS, pS, jS, pre_all, pre_in, ev_k, ev_dst, L.poff,
+        k_seq_apply<<<grid1d(nq), 256, 0, s>>>(nq, eS, pS, jS, head, gidx, gstart, pre_all, pre_in,
+                                               ev_k, ev_dst, L.poff,
                                                R.nrun, R.rpart, R.rcnt, R.rcin, ew, gseq, lose, gin);
         count_launch();
     }
@@ -665,17 +676,12 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     if (!e) e = inclusive_scan_i64(tmp, v64, viol, M, s);
     if (e) return e;
     int32_t *dk;
-    long long *dg;
     e = dalloc(tmp, &dk, 1);
-    if (!e) e = dalloc(tmp, &dg, 1);
     if (e) return e;
-    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, dg);
+    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, d_stats, d_applied);
     count_launch();
     k_apply<<<grid1d(M), 256, 0, s>>>(M, dk, mv_n, mv_pd, rho);
     count_launch();
-    e = cudaMemcpyAsync(&out->kstar, dk, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaMemcpyAsync(&out->gain, dg, sizeof(long long), cudaMemcpyDeviceToHost, s);
-    if (e) return e;
     return cudaGetLastError();
 }
 
