@@ -19,10 +19,11 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
                          const int32_t *pair, const int32_t *score, int32_t *status,
                          cudaStream_t s);
 int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
-                     cudaError_t *cerr, std::string *why, cudaStream_t s);
-cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
-                            int32_t K, int64_t omega, int64_t delta, long long *d_stats,
-                            unsigned long long *d_applied, uint32_t debug, cudaStream_t s);
+                     int64_t *wsum_e, cudaError_t *cerr, std::string *why, cudaStream_t s);
+cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
+                            int32_t *rho, int32_t K, int64_t omega, int64_t delta,
+                            long long *d_stats, unsigned long long *d_applied, uint32_t debug,
+                            cudaStream_t s);
 void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
                  cudaStream_t s);
 cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
@@ -56,6 +57,7 @@ struct hgp_graph {
     int32_t *ew = nullptr;
     int32_t N = 0, E = 0;
     int64_t W = 0;
+    int64_t wsum_e = 0;          // total edge weight (bounds every gain)
     int32_t max_w = 0, max_in = 0;
     std::string err;
     hgp_stats stats{};
@@ -159,7 +161,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     tmp.stream = s;
     cudaError_t ce = cudaSuccess;
     std::string why;
-    int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, &ce, &why, s);
+    int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, &g->wsum_e, &ce, &why, s);
     if (rc != 0) {
         tmp.release_all();
         if (rc < 0) return bail(cuda_fail(g, ce, "build level 0"));
@@ -380,8 +382,8 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         const Level &Lv = levels[l];
         if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
         for (int p = 0; p < passes; ++p) {
-            CKP(run_refine_pass(tmp, Lv, g->ew, rho, K, omega, delta, d_rstat + 3 * l, d_applied,
-                                debug, s), "refine");
+            CKP(run_refine_pass(tmp, Lv, g->ew, g->wsum_e, rho, K, omega, delta, d_rstat + 3 * l,
+                                d_applied, debug, s), "refine");
             tmp.reset();
         }
         if (debug & HGP_DEBUG_KEEP_LEVELS) {

@@ -91,7 +91,7 @@ static int grid1d(int64_t n) {
 // Returns 0 on success, or the failing rule code (> 0), or -1 on CUDA error
 // (then *cerr holds it).
 int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
-                     cudaError_t *cerr, std::string *why, cudaStream_t s) {
+                     int64_t *wsum_e, cudaError_t *cerr, std::string *why, cudaStream_t s) {
     *cerr = cudaSuccess;
     ValidateOut *dv = nullptr;
     cudaError_t e = dalloc(tmp, &dv, 1);
@@ -112,6 +112,7 @@ int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, co
         return hv.bad;
     }
     if (hv.esum > 0x7fffffffull) { *why = "sum of edge weights must be < 2^31"; return 6; }
+    *wsum_e = (int64_t)hv.esum;
     int64_t P = h_P;
     L.P = P;
     k_validate_nodes<<<grid1d(P > N ? P : N), 256, 0, s>>>(N, P, L.pins, L.w, dv);

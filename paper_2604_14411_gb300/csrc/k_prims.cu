@@ -98,11 +98,26 @@ __global__ void k_tile_sums(const T *in, int64_t n, T *sums) {
 }
 
 template <typename T, bool Inclusive>
-__global__ void k_tile_scan(const T *in, T *out, int64_t n, const T *tile_offsets, T *total) {
+__global__ void k_tile_scan(const T *in, T *out, int64_t n, const T *tile_offsets, T *total,
+                            const T *tile_sums) {
     __shared__ T tile[kScanTile];
     __shared__ T wt[kScanThreads / 32];
     __shared__ T btot;
+    __shared__ T s_off;
     int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (tile_sums) {               // offset of this tile = sum of the earlier tiles' sums
+        T acc = 0;
+        for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) acc += tile_sums[t];
+        acc = warp_sum(acc);
+        if (lane_id() == 0) wt[warp_id()] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T o = 0;
+            for (int w = 0; w < kScanThreads / 32; ++w) o += wt[w];
+            s_off = o;
+        }
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
         int64_t j = base + i;
         tile[i] = j < n ? in[j] : T(0);
@@ -116,7 +131,7 @@ __global__ void k_tile_scan(const T *in, T *out, int64_t n, const T *tile_offset
         s += loc[k];
     }
     T pre = block_exclusive_scan<T>(s, wt, &btot);
-    T off = tile_offsets ? tile_offsets[blockIdx.x] : T(0);
+    T off = tile_sums ? s_off : (tile_offsets ? tile_offsets[blockIdx.x] : T(0));
     T run = off + pre;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -138,19 +153,21 @@ static cudaError_t scan_impl(Arena &a, const T *in, T *out, int64_t n, T *total,
         return cudaSuccess;
     }
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    T *offs = nullptr;
+    T *offs = nullptr, *sums = nullptr;
     if (tiles > 1) {
-        T *sums = nullptr;
         cudaError_t e = dalloc(a, &sums, tiles);
-        if (e) return e;
-        e = dalloc(a, &offs, tiles);
         if (e) return e;
         k_tile_sums<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
         count_launch();
-        e = scan_impl<T, false>(a, sums, offs, tiles, (T *)nullptr, s);
-        if (e) return e;
+        if (tiles > 4096) {        // many tiles: scan the tile sums recursively
+            e = dalloc(a, &offs, tiles);
+            if (e) return e;
+            e = scan_impl<T, false>(a, sums, offs, tiles, (T *)nullptr, s);
+            if (e) return e;
+            sums = nullptr;
+        }
     }
-    k_tile_scan<T, Inclusive><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs, total);
+    k_tile_scan<T, Inclusive><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs, total, sums);
     count_launch();
     return cudaGetLastError();
 }

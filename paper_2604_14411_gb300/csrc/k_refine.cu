@@ -62,7 +62,25 @@ __global__ void k_pin_parts(int64_t P, const int32_t *pins, const int32_t *rho,
     }
 }
 
-__global__ void k_runs(int32_t E, const int32_t *poff, const int32_t *parts_sorted,
+// Parts of each edge's pins after sorting; with a combined key the part is
+// key - e * K, otherwise the sorted parts are given directly.
+struct PartsView {
+    const int32_t *parts;      // two-sort path
+    const uint32_t *ekp;       // combined-key path
+    int32_t K;
+    __device__ __forceinline__ int32_t at(int64_t e, int32_t j) const {
+        return parts ? parts[j] : (int32_t)(ekp[j] - (uint32_t)e * (uint32_t)K);
+    }
+};
+
+__global__ void k_pin_ekp(int64_t P, const int32_t *pins, const int32_t *rho, const int32_t *row_of,
+                          int32_t K, uint32_t *key) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x)
+        key[j] = (uint32_t)row_of[j] * (uint32_t)K + (uint32_t)rho[pins[j]];
+}
+
+__global__ void k_runs(int32_t E, const int32_t *poff, PartsView pv,
                        const int32_t *src, const uint8_t *sdst, const int32_t *rho,
                        int32_t *rpart, int32_t *rcnt, int32_t *rcin, int32_t *rpos,
                        int32_t *nrun, int32_t *inb) {
@@ -77,8 +95,8 @@ __global__ void k_runs(int32_t E, const int32_t *poff, const int32_t *parts_sort
             bool st = false;
             int32_t p = 0;
             if (j < p1) {
-                p = parts_sorted[j];
-                st = (j == p0) || parts_sorted[j - 1] != p;
+                p = pv.at(e, j);
+                st = (j == p0) || pv.at(e, j - 1) != p;
             }
             unsigned ball = __ballot_sync(0xffffffffu, st);
             if (st) {
@@ -111,15 +129,8 @@ struct Runs {
 static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, int32_t K,
                               Runs &R, int32_t *inb, cudaStream_t s) {
     int64_t P = L.P;
-    int32_t *row_of, *ve, *ve2, *ps2, *rpos;
-    uint32_t *kp, *kp2, *ke2;
+    int32_t *row_of, *rpos;
     cudaError_t e = dalloc(tmp, &row_of, P);
-    if (!e) e = dalloc(tmp, &kp, P);
-    if (!e) e = dalloc(tmp, &ve, P);
-    if (!e) e = dalloc(tmp, &kp2, P);
-    if (!e) e = dalloc(tmp, &ve2, P);
-    if (!e) e = dalloc(tmp, &ke2, P);
-    if (!e) e = dalloc(tmp, &ps2, P);
     if (!e) e = dalloc(tmp, &rpos, P);
     if (!e) e = dalloc(tmp, &R.rpart, P);
     if (!e) e = dalloc(tmp, &R.rcnt, P);
@@ -127,18 +138,45 @@ static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, in
     if (!e) e = dalloc(tmp, &R.nrun, L.E);
     if (e) return e;
     expand_rows(L.poff, L.E, row_of, s);
-    if (P > 0) {
-        k_pin_parts<<<grid1d(P), 256, 0, s>>>(P, L.pins, rho, row_of, kp, ve);
-        count_launch();
+    PartsView pv{nullptr, nullptr, K};
+    if ((int64_t)L.E * K <= (int64_t)UINT32_MAX) {
+        // one stable sort of (edge * K + part): each edge's segment sorted by part
+        uint32_t *k1, *k2;
+        e = dalloc(tmp, &k1, P);
+        if (!e) e = dalloc(tmp, &k2, P);
+        if (e) return e;
+        if (P > 0) {
+            k_pin_ekp<<<grid1d(P), 256, 0, s>>>(P, L.pins, rho, row_of, K, k1);
+            count_launch();
+        }
+        e = radix_sort_pairs(tmp, k1, nullptr, k2, nullptr, P,
+                             bits_for((int64_t)L.E * K > 0 ? (int64_t)L.E * K - 1 : 0), s);
+        if (e) return e;
+        pv.ekp = k2;
+    } else {
+        // stable by part, then stable by edge
+        int32_t *ve, *ve2, *ps2;
+        uint32_t *kp, *kp2, *ke2;
+        e = dalloc(tmp, &kp, P);
+        if (!e) e = dalloc(tmp, &ve, P);
+        if (!e) e = dalloc(tmp, &kp2, P);
+        if (!e) e = dalloc(tmp, &ve2, P);
+        if (!e) e = dalloc(tmp, &ke2, P);
+        if (!e) e = dalloc(tmp, &ps2, P);
+        if (e) return e;
+        if (P > 0) {
+            k_pin_parts<<<grid1d(P), 256, 0, s>>>(P, L.pins, rho, row_of, kp, ve);
+            count_launch();
+        }
+        e = radix_sort_pairs(tmp, kp, ve, kp2, ve2, P, bits_for(K > 0 ? K - 1 : 0), s);
+        if (!e) e = radix_sort_pairs(tmp, reinterpret_cast<uint32_t *>(ve2),
+                                     reinterpret_cast<int32_t *>(kp2), ke2, ps2, P,
+                                     bits_for(L.E > 0 ? L.E - 1 : 0), s);
+        if (e) return e;
+        pv.parts = ps2;
     }
-    // stable by part, then stable by edge: each edge's segment sorted by part
-    e = radix_sort_pairs(tmp, kp, ve, kp2, ve2, P, bits_for(K > 0 ? K - 1 : 0), s);
-    if (!e) e = radix_sort_pairs(tmp, reinterpret_cast<uint32_t *>(ve2),
-                                 reinterpret_cast<int32_t *>(kp2), ke2, ps2, P,
-                                 bits_for(L.E > 0 ? L.E - 1 : 0), s);
-    if (e) return e;
     if (L.E > 0) {
-        k_runs<<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, ps2, L.src, L.sdst, rho, R.rpart,
+        k_runs<<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, pv, L.src, L.sdst, rho, R.rpart,
                                                R.rcnt, R.rcin, rpos, R.nrun, inb);
         count_launch();
     }
@@ -233,13 +271,13 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
 
 // ---------------------------------------------------------------- sequence
 __global__ void k_move_keys(int32_t V, const int32_t *gain, const int32_t *rank, uint32_t *key,
-                            int32_t *node) {
+                            int32_t *node, int64_t wsum) {
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
          n += (int64_t)gridDim.x * blockDim.x) {
         int32_t g = gain[n];
         if (g > 0) {
             int32_t r = rank[n];
-            key[r] = (uint32_t)(0x7fffffff - g);     // ascending key = descending gain
+            key[r] = (uint32_t)(wsum - g);     // ascending key = descending gain (1 <= g <= wsum)
             node[r] = (int32_t)n;
         }
     }
@@ -298,6 +336,19 @@ __global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_p
             ev_id[j + 1] = j + 1;
         }
     }
+}
+
+__global__ void k_event_ekp(int64_t n, const int32_t *ev_e, const uint32_t *ev_p, int32_t K,
+                            uint32_t *key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = (uint32_t)ev_e[i] * (uint32_t)K + ev_p[i];
+}
+
+__global__ void k_key_edge(int64_t n, const uint32_t *key, int32_t K, uint32_t *edge) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        edge[i] = key[i] / (uint32_t)K;
 }
 
 __global__ void k_gather_u32(int64_t n, const int32_t *src, const int32_t *idx, uint32_t *out) {
@@ -494,9 +545,10 @@ __global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
 
 // One refinement pass on level L; rho is updated in place on the device.
 // d_stats (device, 3 x int64) receives (M, k*, gain); *d_applied adds k*.
-cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32_t *rho,
-                            int32_t K, int64_t omega, int64_t delta, long long *d_stats,
-                            unsigned long long *d_applied, uint32_t debug, cudaStream_t s) {
+cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
+                            int32_t *rho, int32_t K, int64_t omega, int64_t delta,
+                            long long *d_stats, unsigned long long *d_applied, uint32_t debug,
+                            cudaStream_t s) {
     int32_t V = L.V;
     int32_t *size, *inb;
     cudaError_t e = dalloc(tmp, &size, K);
@@ -565,9 +617,9 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
     if (!e) e = dalloc(tmp, &lose, M);
     if (!e) e = dalloc(tmp, &gin, M);
     if (e) return e;
-    k_move_keys<<<grid1d(V), 256, 0, s>>>(V, pg, rank, mkey, mnode);
+    k_move_keys<<<grid1d(V), 256, 0, s>>>(V, pg, rank, mkey, mnode, wsum);
     count_launch();
-    e = radix_sort_pairs(tmp, mkey, mnode, mkey2, mv_n, M, 31, s);
+    e = radix_sort_pairs(tmp, mkey, mnode, mkey2, mv_n, M, bits_for(wsum), s);
     if (e) return e;
     fill_i32(idx_of, -1, V, s);
     k_move_info<<<grid1d(M), 256, 0, s>>>(M, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
@@ -610,13 +662,23 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int32
         k_seq_events<<<grid_warps(M), 256, 0, s>>>(M, mv_n, mv_ps, mv_pd, L.ioff, L.inc, L.src,
                                                    L.sdst, evoff, ev_p, ev_e, ev_k, ev_dst, ev_id);
         count_launch();
-        // stable by part, then stable by edge: grouped by (e, p), move order inside
-        e = radix_sort_pairs(tmp, ev_p, ev_id, p1, j1, nq, bits_for(K > 0 ? K - 1 : 0), s);
-        if (e) return e;
-        k_gather_u32<<<grid1d(nq), 256, 0, s>>>(nq, ev_e, j1, e1);
-        count_launch();
-        e = radix_sort_pairs(tmp, e1, j1, eS, jS, nq, bits_for(L.E > 0 ? L.E - 1 : 0), s);
-        if (e) return e;
+        // grouped by (e, p), move order inside each group
+        if ((int64_t)L.E * K <= (int64_t)UINT32_MAX) {
+            k_event_ekp<<<grid1d(nq), 256, 0, s>>>(nq, ev_e, ev_p, K, p1);
+            count_launch();
+            e = radix_sort_pairs(tmp, p1, ev_id, e1, jS, nq,
+                                 bits_for((int64_t)L.E * K > 0 ? (int64_t)L.E * K - 1 : 0), s);
+            if (e) return e;
+            k_key_edge<<<grid1d(nq), 256, 0, s>>>(nq, e1, K, eS);
+            count_launch();
+        } else {    // stable by part, then stable by edge
+            e = radix_sort_pairs(tmp, ev_p, ev_id, p1, j1, nq, bits_for(K > 0 ? K - 1 : 0), s);
+            if (e) return e;
+            k_gather_u32<<<grid1d(nq), 256, 0, s>>>(nq, ev_e, j1, e1);
+            count_launch();
+            e = radix_sort_pairs(tmp, e1, j1, eS, jS, nq, bits_for(L.E > 0 ? L.E - 1 : 0), s);
+            if (e) return e;
+        }
         int32_t *head, *gidx, *gstart;
         e = dalloc(tmp, &head, nq);
         if (!e) e = dalloc(tmp, &gidx, nq);
