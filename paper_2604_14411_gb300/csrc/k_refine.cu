@@ -209,17 +209,30 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         int32_t ps = a.rho[n];
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
         long long sav = 0, wI = 0;
-        for (int32_t k = i0 + warp_id(); k < i1; k += kPropWarps) {
-            int32_t e = a.inc[k];
-            int32_t we = a.ew[e];
-            int32_t r0 = a.poff[e], r1 = r0 + a.nrun[e];
-            if (lane_id() == 0) wI += we;
-            for (int32_t q = r0 + lane_id(); q < r1; q += 32) {
-                int32_t p = a.rpart[q];
-                if (p == ps) {
-                    if (a.rcnt[q] == 1) sav += we;
-                } else if (atomicAdd(&pres[p], we) == 0) {
-                    touched[atomicAdd(&s_nt, 1)] = p;
+        // each lane fetches one hyperedge's (omega, run range); the warp walks them
+        int32_t mine = (i1 - i0 - warp_id() + kPropWarps - 1) / kPropWarps;
+        for (int32_t c0 = 0; c0 < mine; c0 += 32) {
+            int32_t k = i0 + warp_id() + kPropWarps * (c0 + lane_id());
+            int32_t we = 0, r0 = 0, r1 = 0;
+            if (c0 + lane_id() < mine) {
+                int32_t e = a.inc[k];
+                we = a.ew[e];
+                r0 = a.poff[e];
+                r1 = r0 + a.nrun[e];
+                wI += we;
+            }
+            int32_t cnt = min(32, mine - c0);
+            for (int32_t t = 0; t < cnt; ++t) {
+                int32_t wt = __shfl_sync(0xffffffffu, we, t);
+                int32_t b0 = __shfl_sync(0xffffffffu, r0, t);
+                int32_t b1 = __shfl_sync(0xffffffffu, r1, t);
+                for (int32_t q = b0 + lane_id(); q < b1; q += 32) {
+                    int32_t p = a.rpart[q];
+                    if (p == ps) {
+                        if (a.rcnt[q] == 1) sav += wt;
+                    } else if (atomicAdd(&pres[p], wt) == 0) {
+                        touched[atomicAdd(&s_nt, 1)] = p;
+                    }
                 }
             }
         }

@@ -148,29 +148,44 @@ k_score(ScoreArgs a) {
         }
         __syncthreads();
         // ---- Eq. (2) accumulation ----
+        // each lane fetches one hyperedge's (omega, pin range); the warp then
+        // walks those 32 hyperedges, its lanes reading each one's pins
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
-        for (int32_t k = i0 + warp_id(); k < i1; k += kScoreWarps) {
-            int32_t e = a.inc[k];
-            int32_t we = a.ew[e];
-            int32_t p0 = a.poff[e], p1 = a.poff[e + 1];
-            for (int32_t j = p0 + lane_id(); j < p1; j += 32) {
-                int32_t m = a.pins[j];
-                if (m == n) continue;
-                if (DENSE) {
-                    atomicAdd(&hist[m], we);
-                } else {
-                    uint32_t slot = hash_u32((uint32_t)m) & mask;
-                    int32_t probes = 0;
-                    for (;;) {
-                        int32_t k0 = atomicCAS(&gkeys[slot], -1, m);
-                        if (k0 == -1 || k0 == m) { atomicAdd(&gvals[slot], we); break; }
-                        slot = (slot + 1) & mask;
-                        if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
+        // warp w takes hyperedges i0 + w, i0 + w + W, ... (W warps), 32 per round
+        int32_t mine = (i1 - i0 - warp_id() + kScoreWarps - 1) / kScoreWarps;
+        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
+            int32_t k = i0 + warp_id() + kScoreWarps * (r0 + lane_id());
+            int32_t we = 0, p0 = 0, p1 = 0;
+            if (r0 + lane_id() < mine) {
+                int32_t e = a.inc[k];
+                we = a.ew[e];
+                p0 = a.poff[e];
+                p1 = a.poff[e + 1];
+            }
+            int32_t cnt = min(32, mine - r0);
+            for (int32_t t = 0; t < cnt; ++t) {
+                int32_t wt = __shfl_sync(0xffffffffu, we, t);
+                int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
+                int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
+                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
+                    int32_t m = a.pins[j];
+                    if (m == n) continue;
+                    if (DENSE) {
+                        atomicAdd(&hist[m], wt);
+                    } else {
+                        uint32_t slot = hash_u32((uint32_t)m) & mask;
+                        int32_t probes = 0;
+                        for (;;) {
+                            int32_t kk = atomicCAS(&gkeys[slot], -1, m);
+                            if (kk == -1 || kk == m) { atomicAdd(&gvals[slot], wt); break; }
+                            slot = (slot + 1) & mask;
+                            if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
+                        }
                     }
                 }
+                if (lane_id() == 0)
+                    bytes += 16ull + 4ull * (unsigned long long)(b1 - b0);  // inc, omega, 2 offsets, pins
             }
-            if (lane_id() == 0)
-                bytes += 16ull + 4ull * (unsigned long long)(p1 - p0);  // inc, omega, 2 offsets, pins
         }
         __syncthreads();
         // ---- extraction by decreasing hist value ----
