@@ -3,11 +3,12 @@
 // Every coarse node c is one node or one matched pair {a, b} (a < b), so the
 // set unions of the paper are unions of at most two sorted lists:
 //   I'(c)  = I(a) u I(b)       in'(c) = in(a) u in(b)
-// A warp per coarse node merges the two sorted lists with duplicates removed:
-// each element finds its output slot from a binary search in the other list
-// and a ballot-prefix count of the duplicates before it, so the result is
-// sorted without any sort.  The lengths are counted first, prefix-summed into
-// the new offsets, then written.
+// Unmatched nodes keep their lists (counted and copied by whole CTAs).  A CTA
+// per matched pair merges the two sorted lists with duplicates removed, both
+// staged in shared memory: each element finds its output slot from a binary
+// search in the other list and a CTA-wide ballot prefix of the duplicates
+// before it, so the result is sorted without any sort.  The lengths are
+// counted first, prefix-summed into the new offsets, then written.
 // pins'(e) = gamma(pins(e)) as a set: a pin is dropped only when it is the
 // larger member b of a pair whose smaller member a is also a pin of e (tested
 // by a binary search of e in the sorted I(a)); the rest are mapped through
@@ -30,75 +31,124 @@ __global__ void k_coarse_nodes(int32_t V, const int32_t *match, const int32_t *g
     }
 }
 
-// |A u B| (count) or the merged list (write), warp-cooperative.
+// |A u B| (count) or the merged sorted list (write), CTA-cooperative: each
+// element's output slot is its index plus its rank in the other list minus
+// the duplicates before it (a CTA-wide ballot prefix).
 template <bool WRITE>
-__device__ int32_t warp_union(const int32_t *A, int32_t na, const int32_t *B, int32_t nb,
-                              int32_t *out) {
+__device__ int32_t block_union(const int32_t *A, int32_t na, const int32_t *B, int32_t nb,
+                               int32_t *out, int32_t *s_w) {
+    const int nw = blockDim.x >> 5;
     unsigned lt = (1u << lane_id()) - 1u;
     int32_t dupA = 0;
-    for (int32_t base = 0; base < na; base += 32) {
-        int32_t i = base + lane_id();
+    for (int32_t base = 0; base < na; base += blockDim.x) {
+        int32_t i = base + threadIdx.x;
         bool valid = i < na;
         int32_t x = valid ? A[i] : 0;
         int32_t lb = valid ? lower_bound_i32(B, 0, nb, x) : 0;
         bool inB = valid && lb < nb && B[lb] == x;
         unsigned ball = __ballot_sync(0xffffffffu, inB);
-        if (WRITE && valid) out[i + lb - (dupA + __popc(ball & lt))] = x;
-        dupA += __popc(ball);
+        if (lane_id() == 0) s_w[warp_id()] = __popc(ball);
+        __syncthreads();
+        int32_t pre = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) { pre += q < warp_id() ? s_w[q] : 0; tot += s_w[q]; }
+        if (WRITE && valid) out[i + lb - (dupA + pre + __popc(ball & lt))] = x;
+        dupA += tot;
+        __syncthreads();
     }
     if (!WRITE) return na + nb - dupA;
     int32_t dupB = 0;
-    for (int32_t base = 0; base < nb; base += 32) {
-        int32_t j = base + lane_id();
+    for (int32_t base = 0; base < nb; base += blockDim.x) {
+        int32_t j = base + threadIdx.x;
         bool valid = j < nb;
         int32_t y = valid ? B[j] : 0;
         int32_t lb = valid ? lower_bound_i32(A, 0, na, y) : 0;
         bool inA = valid && lb < na && A[lb] == y;
         unsigned ball = __ballot_sync(0xffffffffu, inA);
-        if (valid && !inA) out[lb + j - (dupB + __popc(ball & lt))] = y;
-        dupB += __popc(ball);
+        if (lane_id() == 0) s_w[warp_id()] = __popc(ball);
+        __syncthreads();
+        int32_t pre = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) { pre += q < warp_id() ? s_w[q] : 0; tot += s_w[q]; }
+        if (valid && !inA) out[lb + j - (dupB + pre + __popc(ball & lt))] = y;
+        dupB += tot;
+        __syncthreads();
     }
     return na + nb - dupA;
 }
 
-// Count pass: a warp per coarse node; unmatched nodes keep their lists.
+// Count pass for unmatched nodes (their lists are kept); matched pairs are
+// queued for k_union_merged.
 __global__ void k_union_count(int32_t V2, const int32_t *rep_of, const int32_t *match,
-                              const int32_t *ioff, const int32_t *inc, const int32_t *noff,
-                              const int32_t *inn, int32_t *cntI, int32_t *cntN, int32_t *max_in) {
-    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = gw; c < V2; c += nw) {
-        int32_t a = rep_of[c], b = match[a];
-        int32_t nIa = ioff[a + 1] - ioff[a], nNa = noff[a + 1] - noff[a];
-        int32_t ci = nIa, cn = nNa;
-        if (b != a) {
-            ci = warp_union<false>(inc + ioff[a], nIa, inc + ioff[b], ioff[b + 1] - ioff[b], nullptr);
-            cn = warp_union<false>(inn + noff[a], nNa, inn + noff[b], noff[b + 1] - noff[b], nullptr);
+                              const int32_t *ioff, const int32_t *noff, int32_t *cntI,
+                              int32_t *cntN, int32_t *max_in, int32_t *mlist, int32_t *mcount) {
+    int32_t mi = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < V2;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = rep_of[c];
+        if (match[a] == a) {
+            cntI[c] = ioff[a + 1] - ioff[a];
+            cntN[c] = noff[a + 1] - noff[a];
+            mi = max(mi, cntN[c]);
+        } else {
+            mlist[atomicAdd(mcount, 1)] = (int32_t)c;
         }
-        if (lane_id() == 0) { cntI[c] = ci; cntN[c] = cn; atomicMax(max_in, cn); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mi = max(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+    if (lane_id() == 0 && mi) atomicMax(max_in, mi);
+}
+
+// Matched pairs: a CTA per pair, both lists staged in shared memory when
+// they fit (binary searches then stay on chip).
+template <bool WRITE>
+__global__ void k_union_merged(const int32_t *mlist, const int32_t *mcount, const int32_t *rep_of,
+                               const int32_t *match, const int32_t *ioff, const int32_t *inc,
+                               const int32_t *noff, const int32_t *inn, int32_t *cntI,
+                               int32_t *cntN, int32_t *max_in, const int32_t *ioff2, int32_t *inc2,
+                               const int32_t *noff2, int32_t *inn2, int32_t cap) {
+    extern __shared__ int32_t stage[];
+    __shared__ int32_t s_w[32];
+    int32_t nm = *mcount;
+    for (int32_t t = blockIdx.x; t < nm; t += gridDim.x) {
+        int32_t c = mlist[t], a = rep_of[c], b = match[a];
+        int32_t res[2];
+        for (int which = 0; which < 2; ++which) {
+            const int32_t *off = which ? noff : ioff;
+            const int32_t *dat = which ? inn : inc;
+            const int32_t *A = dat + off[a], *B = dat + off[b];
+            int32_t na = off[a + 1] - off[a], nb = off[b + 1] - off[b];
+            if (na + nb <= cap) {
+                for (int32_t i = threadIdx.x; i < na; i += blockDim.x) stage[i] = A[i];
+                for (int32_t i = threadIdx.x; i < nb; i += blockDim.x) stage[na + i] = B[i];
+                __syncthreads();
+                A = stage;
+                B = stage + na;
+            }
+            int32_t *out = nullptr;
+            if (WRITE) out = which ? inn2 + noff2[c] : inc2 + ioff2[c];
+            res[which] = block_union<WRITE>(A, na, B, nb, out, s_w);
+            __syncthreads();
+        }
+        if (!WRITE && threadIdx.x == 0) {
+            cntI[c] = res[0];
+            cntN[c] = res[1];
+            atomicMax(max_in, res[1]);
+        }
     }
 }
 
-// Write pass: a CTA per coarse node; unmatched nodes are copied by the whole
-// CTA, matched pairs are merged by its first warp.
-__global__ void k_union_write(int32_t V2, const int32_t *rep_of, const int32_t *match,
-                              const int32_t *ioff, const int32_t *inc, const int32_t *noff,
-                              const int32_t *inn, const int32_t *ioff2, int32_t *inc2,
-                              const int32_t *noff2, int32_t *inn2) {
+// Write pass for unmatched nodes: the whole CTA copies the kept lists.
+__global__ void k_union_copy(int32_t V2, const int32_t *rep_of, const int32_t *match,
+                             const int32_t *ioff, const int32_t *inc, const int32_t *noff,
+                             const int32_t *inn, const int32_t *ioff2, int32_t *inc2,
+                             const int32_t *noff2, int32_t *inn2) {
     for (int32_t c = blockIdx.x; c < V2; c += gridDim.x) {
-        int32_t a = rep_of[c], b = match[a];
-        if (b == a) {
-            int32_t i0 = ioff[a], n0 = noff[a];
-            int32_t ni = ioff[a + 1] - i0, nn = noff[a + 1] - n0;
-            int32_t *oi = inc2 + ioff2[c], *on = inn2 + noff2[c];
-            for (int32_t t = threadIdx.x; t < ni; t += blockDim.x) oi[t] = inc[i0 + t];
-            for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) on[t] = inn[n0 + t];
-        } else if (threadIdx.x < 32) {
-            warp_union<true>(inc + ioff[a], ioff[a + 1] - ioff[a], inc + ioff[b], ioff[b + 1] - ioff[b],
-                             inc2 + ioff2[c]);
-            warp_union<true>(inn + noff[a], noff[a + 1] - noff[a], inn + noff[b], noff[b + 1] - noff[b],
-                             inn2 + noff2[c]);
-        }
+        int32_t a = rep_of[c];
+        if (match[a] != a) continue;
+        int32_t i0 = ioff[a], n0 = noff[a];
+        int32_t ni = ioff[a + 1] - i0, nn = noff[a + 1] - n0;
+        int32_t *oi = inc2 + ioff2[c], *on = inn2 + noff2[c];
+        for (int32_t t = threadIdx.x; t < ni; t += blockDim.x) oi[t] = inc[i0 + t];
+        for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) on[t] = inn[n0 + t];
     }
 }
 
@@ -188,9 +238,11 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     H.V = V2;
     H.E = L.E;
     int32_t *rep_of = nullptr, *cntI = nullptr, *cntN = nullptr, *cntP = nullptr, *dmax = nullptr;
+    int32_t *mlist = nullptr;
     e = dalloc(tmp, &rep_of, V2);
-    if (!e) e = dalloc(tmp, &dmax, 1);
-    if (!e) e = cudaMemsetAsync(dmax, 0, sizeof(int32_t), s);
+    if (!e) e = dalloc(tmp, &mlist, V2);
+    if (!e) e = dalloc(tmp, &dmax, 2);          // [0] largest |in'|, [1] matched pairs queued
+    if (!e) e = cudaMemsetAsync(dmax, 0, 2 * sizeof(int32_t), s);
     if (!e) e = dalloc(tmp, &cntI, V2);
     if (!e) e = dalloc(tmp, &cntN, V2);
     if (!e) e = dalloc(tmp, &cntP, L.E);
@@ -212,8 +264,18 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     count_launch();
     e = cudaMemcpyAsync(H.old_id, rep_of, sizeof(int32_t) * (size_t)V2, cudaMemcpyDeviceToDevice, s);
     if (e) return e;
-    k_union_count<<<grid_warps(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff,
-                                                 L.inn, cntI, cntN, dmax);
+    const int32_t cap = 12288;                  // staged list elements (48 KB)
+    const size_t ssm = sizeof(int32_t) * (size_t)cap;
+    int mblocks = num_sms() * 2;
+    k_union_count<<<grid1d(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.noff, cntI, cntN, dmax,
+                                             mlist, dmax + 1);
+    count_launch();
+    e = cudaFuncSetAttribute(k_union_merged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    if (!e) e = cudaFuncSetAttribute(k_union_merged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    if (e) return e;
+    k_union_merged<false><<<mblocks, 256, ssm, s>>>(mlist, dmax + 1, rep_of, L.match, L.ioff, L.inc,
+                                                    L.noff, L.inn, cntI, cntN, dmax, nullptr, nullptr,
+                                                    nullptr, nullptr, cap);
     count_launch();
     k_coarse_pins<false><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
                                                          L.ioff, L.inc, cntP, nullptr, nullptr);
@@ -239,8 +301,12 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (e) return e;
     {
         int blocks = V2 < num_sms() * 16 ? V2 : num_sms() * 16;
-        k_union_write<<<blocks, 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff, L.inn,
-                                             H.ioff, H.inc, H.noff, H.inn);
+        k_union_copy<<<blocks, 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff, L.inn,
+                                            H.ioff, H.inc, H.noff, H.inn);
+        count_launch();
+        k_union_merged<true><<<mblocks, 256, ssm, s>>>(mlist, dmax + 1, rep_of, L.match, L.ioff,
+                                                       L.inc, L.noff, L.inn, nullptr, nullptr,
+                                                       nullptr, H.ioff, H.inc, H.noff, H.inn, cap);
     }
     count_launch();
     k_coarse_pins<true><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,

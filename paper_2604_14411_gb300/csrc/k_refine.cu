@@ -83,7 +83,12 @@ __global__ void k_pin_ekp(int64_t P, const int32_t *pins, const int32_t *rho, co
 __global__ void k_runs(int32_t E, const int32_t *poff, PartsView pv,
                        const int32_t *src, const uint8_t *sdst, const int32_t *rho,
                        int32_t *rpart, int32_t *rcnt, int32_t *rcin, int32_t *rpos,
-                       int32_t *nrun, int32_t *inb) {
+                       int32_t *nrun, int32_t *inb, int32_t K, int32_t use_smem) {
+    extern __shared__ int32_t inb_s[];       // per-CTA inbound counts (use_smem)
+    if (use_smem) {
+        for (int32_t i = threadIdx.x; i < K; i += blockDim.x) inb_s[i] = 0;
+        __syncthreads();
+    }
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned lt = (1u << lane_id()) - 1u;
@@ -116,9 +121,14 @@ __global__ void k_runs(int32_t E, const int32_t *poff, PartsView pv,
             int32_t ci = c - ((p == srcpart && src_only_out) ? 1 : 0);
             rcnt[p0 + q] = c;
             rcin[p0 + q] = ci;
-            if (inb && ci > 0) atomicAdd(&inb[p], 1);
+            if (inb && ci > 0) atomicAdd(use_smem ? &inb_s[p] : &inb[p], 1);
         }
         if (lane_id() == 0) nrun[e] = r;
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < K; i += blockDim.x)
+            if (inb_s[i]) atomicAdd(&inb[i], inb_s[i]);
     }
 }
 
@@ -176,8 +186,12 @@ static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, in
         pv.parts = ps2;
     }
     if (L.E > 0) {
-        k_runs<<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, pv, L.src, L.sdst, rho, R.rpart,
-                                               R.rcnt, R.rcin, rpos, R.nrun, inb);
+        int32_t use_smem = (inb && K <= 16384) ? 1 : 0;
+        size_t smem = use_smem ? sizeof(int32_t) * (size_t)K : 0;
+        int blocks = grid_warps(L.E);
+        if (use_smem && blocks > num_sms() * 4) blocks = num_sms() * 4;   // fewer flushes
+        k_runs<<<blocks, 256, smem, s>>>(L.E, L.poff, pv, L.src, L.sdst, rho, R.rpart, R.rcnt,
+                                         R.rcin, rpos, R.nrun, inb, K, use_smem);
         count_launch();
     }
     return cudaGetLastError();
@@ -399,7 +413,7 @@ __global__ void k_seq_apply(int64_t nev, const uint32_t *eS, const int32_t *pS, 
                             const int32_t *pre_all, const int32_t *pre_in, const int32_t *ev_k,
                             const uint8_t *ev_dst, const int32_t *poff, const int32_t *nrun,
                             const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
-                            const int32_t *ew, int32_t *gseq, int32_t *lose_in, int32_t *gain_in) {
+                            const int32_t *ew, int32_t *c_gain, uint8_t *c_in) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = eS[i];
@@ -413,15 +427,36 @@ __global__ void k_seq_apply(int64_t nev, const uint32_t *eS, const int32_t *pS, 
         int32_t c = c0 + pre_all[i] - pre_all[lo];
         int32_t ci = c0in + pre_in[i] - pre_in[lo];
         int32_t j = jS[i];
-        int32_t k = ev_k[j];
         bool dst = ev_dst[j] != 0;
+        // contribution of event j (stored at its own id; ids of move k are
+        // contiguous, so a per-move reduction needs no atomics)
         if ((j & 1) == 0) {                                  // leaves ps
-            if (c == 1) atomicAdd(&gseq[k], ew[e]);
-            if (dst && ci == 1) atomicAdd(&lose_in[k], 1);
+            c_gain[j] = (c == 1) ? ew[e] : 0;
+            c_in[j] = (dst && ci == 1) ? 1 : 0;              // ps loses an inbound edge
         } else {                                             // enters pd
-            if (c == 0) atomicAdd(&gseq[k], -ew[e]);
-            if (dst && ci == 0) atomicAdd(&gain_in[k], 1);
+            c_gain[j] = (c == 0) ? -ew[e] : 0;
+            c_in[j] = (dst && ci == 0) ? 1 : 0;              // pd gains an inbound edge
         }
+    }
+}
+
+// one warp per move: gain = sum of its events' contributions; lose / gain_in =
+// counts of its leave / enter events that change an inbound set
+__global__ void k_move_reduce(int32_t M, const int32_t *evoff, const int32_t *c_gain,
+                              const uint8_t *c_in, int32_t *gseq, int32_t *lose_in,
+                              int32_t *gain_in) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = gw; k < M; k += nw) {
+        int32_t g = 0, lo = 0, gi = 0;
+        for (int32_t j = evoff[k] + lane_id(); j < evoff[k + 1]; j += 32) {
+            g += c_gain[j];
+            if (j & 1) gi += c_in[j]; else lo += c_in[j];
+        }
+        g = warp_sum(g);
+        lo = warp_sum(lo);
+        gi = warp_sum(gi);
+        if (lane_id() == 0) { gseq[k] = g; lose_in[k] = lo; gain_in[k] = gi; }
     }
 }
 
@@ -705,12 +740,16 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         if (e) return e;
         k_group_starts<<<grid1d(nq), 256, 0, s>>>(nq, head, gidx, gstart);
         count_launch();
-        cudaMemsetAsync(gseq, 0, sizeof(int32_t) * (size_t)M, s);
-        cudaMemsetAsync(lose, 0, sizeof(int32_t) * (size_t)M, s);
-        cudaMemsetAsync(gin, 0, sizeof(int32_t) * (size_t)M, s);
+        int32_t *c_gain;
+        uint8_t *c_in;
+        e = dalloc(tmp, &c_gain, nq);
+        if (!e) e = dalloc(tmp, &c_in, nq);
+        if (e) return e;
         k_seq_apply<<<grid1d(nq), 256, 0, s>>>(nq, eS, pS, jS, head, gidx, gstart, pre_all, pre_in,
-                                               ev_k, ev_dst, L.poff,
-                                               R.nrun, R.rpart, R.rcnt, R.rcin, ew, gseq, lose, gin);
+                                               ev_k, ev_dst, L.poff, R.nrun, R.rpart, R.rcnt, R.rcin,
+                                               ew, c_gain, c_in);
+        count_launch();
+        k_move_reduce<<<grid_warps(M), 256, 0, s>>>(M, evoff, c_gain, c_in, gseq, lose, gin);
         count_launch();
     }
     // prefix validity from per-part events
