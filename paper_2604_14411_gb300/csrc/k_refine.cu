@@ -205,6 +205,7 @@ struct PropArgs {
     int64_t omega;
     int32_t *gain, *pd;
     int32_t *gpres;     // per-CTA global tables when K is large
+    int32_t *next;      // work counter: nodes are taken dynamically
 };
 
 template <bool DENSE>
@@ -216,10 +217,14 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
     // pres(n, p) per part, and the list of parts touched for this node
     int32_t *pres = DENSE ? smem_p : a.gpres + (int64_t)blockIdx.x * 2 * a.K;
     int32_t *touched = pres + a.K;
+    __shared__ int32_t s_n;
     for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
     if (threadIdx.x == 0) s_nt = 0;
-    __syncthreads();
-    for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int32_t n = s_n;
+        if (n >= a.V) break;
         int32_t ps = a.rho[n];
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
         long long sav = 0, wI = 0;
@@ -618,6 +623,9 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     pa.V = V; pa.K = K; pa.w = L.w; pa.ioff = L.ioff; pa.inc = L.inc; pa.poff = L.poff;
     pa.ew = ew; pa.rho = rho; pa.size = size; pa.rpart = R.rpart; pa.rcnt = R.rcnt;
     pa.nrun = R.nrun; pa.omega = omega; pa.gain = pg; pa.pd = ppd;
+    e = dalloc(tmp, &pa.next, 1);
+    if (!e) e = cudaMemsetAsync(pa.next, 0, sizeof(int32_t), s);
+    if (e) return e;
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
         size_t smem = 2 * sizeof(int32_t) * (size_t)K;

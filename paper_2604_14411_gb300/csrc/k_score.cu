@@ -23,7 +23,9 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score; a.status = status; a.bytes = bytes;
     a.dead = L.dead; a.merged = L.merged; a.thr = L.thr; a.old_id = L.old_id;
-    cudaError_t e;
+    cudaError_t e = dalloc(ar, &a.next, 1);
+    if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
+    if (e) return e;
     // bitmaps only when some pair may need a union count
     int32_t words = ((L.E + 31) / 32 + 3) & ~3;
     bool need_union = 2 * (int64_t)L.max_in > delta;

@@ -47,6 +47,7 @@ struct ScoreArgs {
     const uint8_t *dead, *merged;    // carried level state (null at level 0)
     const unsigned long long *thr;
     const int32_t *old_id;
+    int32_t *next;                   // work counter: nodes are taken dynamically
 };
 
 // m is worth checking for n: alive, and either newly merged or ranked below
@@ -130,9 +131,15 @@ k_score(ScoreArgs a) {
     const uint32_t mask = (uint32_t)a.gcap - 1u;
     unsigned long long bytes = 0;
 
-    for (int32_t n = blockIdx.x; n < a.V; n += gridDim.x) {
+    __shared__ int32_t s_n;
+    for (;;) {
+        if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int32_t n = s_n;
+        if (n >= a.V) break;
         if (a.dead && a.dead[n]) {              // no valid candidate can exist
             if (threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; }
+            __syncthreads();
             continue;
         }
         const unsigned long long thr = a.thr ? a.thr[n] : 0ull;

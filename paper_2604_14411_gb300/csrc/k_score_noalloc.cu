@@ -76,8 +76,9 @@ extern "C" int hgp_score_noalloc(int32_t num_nodes, int32_t num_edges, const int
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score;
     a.status = d_max_in + 1;          // the kernel's status word (limits are never hit here)
+    a.next = d_max_in + 2;            // the kernel's node counter
     // largest |in(n)|: union counts (and bitmaps) are needed only if 2 * max > Delta
-    if (cudaMemsetAsync(d_max_in, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return HGP_ERR_CUDA;
+    if (cudaMemsetAsync(d_max_in, 0, 3 * sizeof(int32_t), s) != cudaSuccess) return HGP_ERR_CUDA;
     k_noalloc_max_in<<<num_sms() * 4, 256, 0, s>>>(num_nodes, in_offsets, d_max_in);
     int32_t max_in = 0;
     if (cudaMemcpyAsync(&max_in, d_max_in, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
