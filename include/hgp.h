@@ -146,6 +146,9 @@ typedef struct {
     int64_t kernel_launches;   /* kernels launched by the last hgp_partition */
     int64_t moves_applied;     /* refinement moves applied, all levels */
     int64_t create_launches;   /* kernels launched by hgp_create */
+    double ms_propose;         /* HGP_DEBUG_TIMING: Eq. (3) proposal kernel, summed */
+    int64_t propose_launches;
+    int64_t propose_bytes;     /* algorithmic bytes of all proposal launches */
 } hgp_stats;
 
 /* Statistics of the handle's last hgp_partition (and hgp_create). */

@@ -23,7 +23,7 @@ int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, co
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            cudaStream_t s);
+                            PropTiming *pt, cudaStream_t s);
 void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
                  cudaStream_t s);
 cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
@@ -373,6 +373,9 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         iota_i32(rho, levels[L].V, s);
     long long *d_rstat = nullptr;
     unsigned long long *d_applied = nullptr;
+    PropTiming ptime;
+    CKP(dalloc(lv, &ptime.bytes, 1), "alloc");
+    CKP(cudaMemsetAsync(ptime.bytes, 0, sizeof(unsigned long long), s), "memset");
     CKP(dalloc(lv, &d_rstat, 3 * levels.size()), "alloc");
     CKP(dalloc(lv, &d_applied, 1), "alloc");
     CKP(cudaMemsetAsync(d_rstat, 0, sizeof(long long) * 3 * levels.size(), s), "memset");
@@ -383,7 +386,7 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
         for (int p = 0; p < passes; ++p) {
             CKP(run_refine_pass(tmp, Lv, g->ew, g->wsum_e, rho, K, omega, delta, d_rstat + 3 * l,
-                                d_applied, debug, s), "refine");
+                                d_applied, debug, tm.on ? &ptime : nullptr, s), "refine");
             tmp.reset();
         }
         if (debug & HGP_DEBUG_KEEP_LEVELS) {
@@ -460,7 +463,20 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         unsigned long long b = 0;
         cudaMemcpy(&b, d_bytes, sizeof(b), cudaMemcpyDeviceToHost);
         st.score_bytes = (int64_t)b;
+        double tp = 0;
+        for (auto &pr : ptime.ev) {
+            float ms = 0;
+            cudaEventSynchronize(pr.second);
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            tp += ms;
+        }
+        st.ms_propose = tp;
+        st.propose_launches = (int64_t)ptime.ev.size();
+        unsigned long long pb = 0;
+        cudaMemcpy(&pb, ptime.bytes, sizeof(pb), cudaMemcpyDeviceToHost);
+        st.propose_bytes = (int64_t)pb;
     }
+    for (auto &pr : ptime.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     (void)c0; (void)c1;
     st.kernel_launches = g_launches - launches0;
     cleanup();

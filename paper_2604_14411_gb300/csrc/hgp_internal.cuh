@@ -72,6 +72,12 @@ inline cudaError_t dalloc(Arena &a, T **p, size_t count) {
     return a.alloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
 }
 
+// Event pairs around every proposal launch of a partition (timing runs).
+struct PropTiming {
+    unsigned long long *bytes = nullptr;   // device counter
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+
 // ---------------- launch bookkeeping ----------------
 extern thread_local int64_t g_launches;
 inline void count_launch() { ++g_launches; }

@@ -206,6 +206,7 @@ struct PropArgs {
     int32_t *gain, *pd;
     int32_t *gpres;     // per-CTA global tables when K is large
     int32_t *next;      // work counter: nodes are taken dynamically
+    unsigned long long *bytes;   // algorithmic bytes (timing runs only)
 };
 
 template <bool DENSE>
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
     int32_t *pres = DENSE ? smem_p : a.gpres + (int64_t)blockIdx.x * 2 * a.K;
     int32_t *touched = pres + a.K;
     __shared__ int32_t s_n;
+    unsigned long long nbytes = 0;
     for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
     if (threadIdx.x == 0) s_nt = 0;
     for (;;) {
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
                 wI += we;
             }
             int32_t cnt = min(32, mine - c0);
+            if (a.bytes && c0 + lane_id() < mine) nbytes += 16ull + 4ull * (unsigned long long)(r1 - r0);
             for (int32_t t = 0; t < cnt; ++t) {
                 int32_t wt = __shfl_sync(0xffffffffu, we, t);
                 int32_t b0 = __shfl_sync(0xffffffffu, r0, t);
@@ -296,8 +299,13 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
             a.gain[n] = g;
             a.pd[n] = pd;
             s_nt = 0;
+            nbytes += 8ull + 12ull;   // gain/pd writes; rho, w, I(n) offsets
         }
         __syncthreads();
+    }
+    if (a.bytes) {
+        nbytes = warp_sum(nbytes);
+        if (lane_id() == 0 && nbytes) atomicAdd(a.bytes, nbytes);
     }
 }
 
@@ -601,7 +609,7 @@ __global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            cudaStream_t s) {
+                            PropTiming *pt, cudaStream_t s) {
     int32_t V = L.V;
     int32_t *size, *inb;
     cudaError_t e = dalloc(tmp, &size, K);
@@ -626,6 +634,13 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     e = dalloc(tmp, &pa.next, 1);
     if (!e) e = cudaMemsetAsync(pa.next, 0, sizeof(int32_t), s);
     if (e) return e;
+    pa.bytes = pt ? pt->bytes : nullptr;
+    if (pt) {
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        cudaEventRecord(ev, s);
+        pt->ev.push_back({ev, nullptr});
+    }
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
         size_t smem = 2 * sizeof(int32_t) * (size_t)K;
@@ -645,6 +660,10 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         k_propose<false><<<blocks, kPropThreads, 0, s>>>(pa);
     }
     count_launch();
+    if (pt) {
+        cudaEventCreate(&pt->ev.back().second);
+        cudaEventRecord(pt->ev.back().second, s);
+    }
     // compact proposals in node order, read M
     int32_t *flag, *rank, *dM;
     e = dalloc(tmp, &flag, V);
