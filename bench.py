@@ -98,6 +98,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_ms(local_ms: float, dist=None, device=None) -> float:
+    """Timed region of the whole job: the maximum over ranks of each rank's
+    summed step time (ranks run independent replicas)."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step: int, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks / job time."""
+    return units_per_step * steps * world / (job_ms / 1000.0)
+
+
 def oracle_sample(steps=1):
     """Times the CPU oracle on the bounded sample; returns (pins/s, seconds)."""
     import oracle
@@ -219,13 +235,9 @@ def main():
     clocks = sampler.stop(local)
     if dist:
         dist.barrier()
-    t_total = sum(times)
-    if dist:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = job_time_ms(sum(times), dist, dev)
     ms_per_step = t_total / args.steps
-    value = P * args.steps * world / (t_total / 1000.0)
+    value = job_value(P, args.steps, world, t_total)
 
     # end to end through the C ABI with pinned host buffers
     h_off = torch.from_numpy(g.offsets.copy()).pin_memory()
