@@ -63,6 +63,8 @@ typedef enum {
                                       paths for scoring and proposals at every level */
 #define HGP_DEBUG_NO_BITMAP 8u     /* test knob: test in(n) membership by binary search instead
                                       of the shared-memory bitmap */
+#define HGP_DEBUG_FORCE_CLUSTER 16u /* test knob: score every level with the 8-CTA cluster
+                                       kernel (distributed shared-memory histogram) */
 
 typedef struct hgp_graph hgp_graph;
 

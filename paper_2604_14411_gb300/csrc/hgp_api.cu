@@ -257,7 +257,7 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         for (int i = 0; i < 6; ++i)
             if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
         if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
-                                     HGP_DEBUG_NO_BITMAP))
+                                     HGP_DEBUG_NO_BITMAP | HGP_DEBUG_FORCE_CLUSTER))
             return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
         passes = opt->refine_passes;
         debug = opt->debug;

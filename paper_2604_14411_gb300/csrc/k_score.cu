@@ -5,6 +5,8 @@
 
 namespace hgp {
 
+bool launch_score_cluster(const ScoreArgs &a, int max_smem, cudaStream_t s, cudaError_t *err);
+
 constexpr int64_t kBitmapBudget = 1ll << 30;   // bytes of in() bitmaps per level
 constexpr int32_t kBitmapMaxWords = 8192;       // 32 KB row in shared memory
 
@@ -45,7 +47,8 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     }
     size_t row_bytes = sizeof(uint32_t) * (size_t)a.bm_words;
     size_t dense_smem = row_bytes + sizeof(int32_t) * (size_t)L.V;
-    bool dense = dense_smem + 2048 <= (size_t)max_smem && !(debug & HGP_DEBUG_FORCE_GLOBAL);
+    bool dense = dense_smem + 2048 <= (size_t)max_smem &&
+                 !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER));
     int sms = num_sms();
     if (dense) {
         e = cudaFuncSetAttribute(k_score<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -59,6 +62,10 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
         k_score<true><<<blocks, kScoreThreads, dense_smem, s>>>(a);
         count_launch();
         return cudaGetLastError();
+    }
+    // levels too large for one CTA: the histogram spread over an 8-CTA cluster
+    if (!(debug & HGP_DEBUG_FORCE_GLOBAL)) {
+        if (launch_score_cluster(a, max_smem, s, &e)) return e ? e : cudaGetLastError();
     }
     // hash mode: per-CTA global tables sized for the heaviest node
     unsigned long long *d_work = nullptr;

@@ -1,0 +1,177 @@
+// Candidate scoring for levels whose node count does not fit one CTA's shared
+// memory: a thread-block cluster of 8 CTAs (8 SMs) holds the Eq. (2)
+// histogram of one node in distributed shared memory, each CTA owning a
+// contiguous slice of node ids.  All 8 CTAs walk the node's hyperedges and add
+// omega(e) into the owning CTA's slice with remote shared-memory atomics; the
+// extraction by decreasing hist value then reduces across the cluster (each
+// CTA checks the tie-group candidates of its own slice).  Same answer as the
+// single-CTA kernel, for up to 8 x ~48k node ids on chip.
+#include <cooperative_groups.h>
+
+#include "k_score.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hgp {
+
+constexpr int kClusterCtas = 8;
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kScoreThreads)
+k_score_cluster(ScoreArgs a, int32_t slice) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
+    int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
+    __shared__ int32_t red[kScoreWarps];
+    __shared__ int32_t s_node, s_xchg, s_bcast;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int32_t id0 = rank * slice;
+    const int32_t len = max(0, min(slice, a.V - id0));
+    unsigned long long bytes = 0;
+
+    for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) hist[i] = 0;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            int32_t t = atomicAdd(a.next, 1);
+            s_node = t < a.V ? t : a.V;
+        }
+        cl.sync();                                   // slices cleared, node published
+        const int32_t n = *cl.map_shared_rank(&s_node, 0);
+        if (n >= a.V) {
+            cl.sync();       // no CTA leaves while a peer may still read its shared memory
+            break;
+        }
+        if (a.dead && a.dead[n]) {
+            if (rank == 0 && threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; }
+            cl.sync();                               // everyone has read s_node
+            continue;
+        }
+        const unsigned long long thr = a.thr ? a.thr[n] : 0ull;
+        if (a.bm_words) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.bm + (int64_t)n * a.bm_words);
+            uint4 *dst = reinterpret_cast<uint4 *>(row_n);
+            for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
+        }
+        // ---- Eq. (2): hyperedges of I(n) interleaved over the cluster's warps ----
+        const int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
+        const int32_t gw = rank * kScoreWarps + warp_id(), nw = kClusterCtas * kScoreWarps;
+        int32_t mine = (i1 - i0 - gw + nw - 1) / nw;
+        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
+            int32_t we = 0, p0 = 0, p1 = 0;
+            if (r0 + lane_id() < mine) {
+                int32_t e = a.inc[i0 + gw + nw * (r0 + lane_id())];
+                we = a.ew[e];
+                p0 = a.poff[e];
+                p1 = a.poff[e + 1];
+            }
+            int32_t cnt = min(32, mine - r0);
+            for (int32_t t = 0; t < cnt; ++t) {
+                int32_t wt = __shfl_sync(0xffffffffu, we, t);
+                int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
+                int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
+                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
+                    int32_t m = a.pins[j];
+                    if (m == n) continue;
+                    int32_t owner = m / slice;
+                    atomicAdd(cl.map_shared_rank(hist, owner) + (m - owner * slice), wt);
+                }
+                if (lane_id() == 0) bytes += 16ull + 4ull * (unsigned long long)(b1 - b0);
+            }
+        }
+        cl.sync();                                   // histogram complete, row(n) staged
+        // ---- extraction by decreasing hist value, reduced over the cluster ----
+        const int64_t in_n = a.noff[n + 1] - a.noff[n];
+        int32_t hcur = 0x7fffffff, result = -1, rscore = 0;
+        for (;;) {
+            int32_t hm = 0;
+            for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) {
+                int32_t h = hist[i];
+                if (h < hcur && h > hm && eligible(a, id0 + i, h, thr)) hm = h;
+            }
+            hm = block_max_i32(hm, red);
+            if (threadIdx.x == 0) s_xchg = hm;
+            cl.sync();
+            if (threadIdx.x == 0) {
+                int32_t v = 0;
+                for (int r = 0; r < kClusterCtas; ++r) v = max(v, *cl.map_shared_rank(&s_xchg, r));
+                s_bcast = v;
+            }
+            cl.sync();                               // all reads of s_xchg done
+            const int32_t hmax = s_bcast;
+            if (hmax == 0) break;
+            int32_t best_id = -1;
+            int32_t per_warp = (((len + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+            int32_t lo = warp_id() * per_warp, hi = min(len, lo + per_warp);
+            for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
+                int32_t i = base + lane_id();
+                bool hit = i < hi && hist[i] == hmax && eligible(a, id0 + i, hmax, thr);
+                unsigned ball = __ballot_sync(0xffffffffu, hit);
+                while (ball && best_id < 0) {
+                    int src = 31 - __clz(ball);
+                    ball &= ~(1u << src);
+                    if (warp_check(a, n, id0 + base + src, row_n, in_n, bytes)) best_id = id0 + base + src;
+                }
+            }
+            best_id = block_max_i32(best_id, red);
+            if (threadIdx.x == 0) s_xchg = best_id;
+            cl.sync();
+            if (threadIdx.x == 0) {
+                int32_t v = -1;
+                for (int r = 0; r < kClusterCtas; ++r) v = max(v, *cl.map_shared_rank(&s_xchg, r));
+                s_bcast = v;
+            }
+            cl.sync();
+            const int32_t win = s_bcast;
+            if (win >= 0) { result = win; rscore = hmax; break; }
+            hcur = hmax;
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            a.pair[n] = result;
+            a.score[n] = result >= 0 ? rscore : 0;
+            bytes += 16ull;
+        }
+        for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) hist[i] = 0;
+        // the cl.sync() at the top of the loop orders these clears before the next adds
+    }
+    if (a.bytes) {
+        bytes = warp_sum(bytes);
+        if (lane_id() == 0 && bytes) atomicAdd(a.bytes, bytes);
+    }
+}
+
+// Launches the cluster kernel if a slice fits on chip; returns false (and
+// launches nothing) otherwise.
+bool launch_score_cluster(const ScoreArgs &a, int max_smem, cudaStream_t s, cudaError_t *err) {
+    *err = cudaSuccess;
+    int32_t slice = (a.V + kClusterCtas - 1) / kClusterCtas;
+    size_t smem = sizeof(uint32_t) * (size_t)a.bm_words + sizeof(int32_t) * (size_t)slice;
+    if (smem + 4096 > (size_t)max_smem) return false;
+    cudaError_t e = cudaFuncSetAttribute(k_score_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) { *err = e; return true; }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kScoreThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kClusterCtas;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cfg.gridDim = dim3(kClusterCtas);
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_score_cluster, &cfg);
+    if (e || clusters < 1) clusters = 1;
+    int want = (a.V + 0) > clusters ? clusters : a.V;
+    cfg.gridDim = dim3(kClusterCtas * want);
+    cfg.attrs = nullptr;       // the cluster shape comes from __cluster_dims__
+    cfg.numAttrs = 0;
+    e = cudaLaunchKernelEx(&cfg, k_score_cluster, a, slice);
+    count_launch();
+    *err = e;
+    return true;
+}
+
+}  // namespace hgp

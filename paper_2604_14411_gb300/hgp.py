@@ -27,6 +27,7 @@ HGP_DEBUG_KEEP_LEVELS = 1
 HGP_DEBUG_TIMING = 2
 HGP_DEBUG_FORCE_GLOBAL = 4
 HGP_DEBUG_NO_BITMAP = 8
+HGP_DEBUG_FORCE_CLUSTER = 16
 (HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
  HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE) = range(8)
 

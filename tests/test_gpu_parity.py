@@ -107,9 +107,15 @@ def test_weighted():
 
 
 @pytest.mark.parametrize("debug", [H.HGP_DEBUG_FORCE_GLOBAL, H.HGP_DEBUG_NO_BITMAP,
-                                   H.HGP_DEBUG_FORCE_GLOBAL | H.HGP_DEBUG_NO_BITMAP])
+                                   H.HGP_DEBUG_FORCE_GLOBAL | H.HGP_DEBUG_NO_BITMAP,
+                                   H.HGP_DEBUG_FORCE_CLUSTER,
+                                   H.HGP_DEBUG_FORCE_CLUSTER | H.HGP_DEBUG_NO_BITMAP])
 def test_fallback_paths(debug):
     compare(synth.random_snn(700, 12, 8), 20, 80, debug=debug)
+
+
+def test_cluster_path_on_the_2k_snn():
+    compare(synth.snn_2k(0), 128, 512, debug=H.HGP_DEBUG_FORCE_CLUSTER)
 
 
 def test_multiple_passes():
