@@ -99,7 +99,10 @@ int hgp_create(int32_t num_nodes, int32_t num_edges,
 typedef struct {
     int32_t refine_passes;     /* refinement passes per level (default 1; 0 = none) */
     uint32_t debug;            /* HGP_DEBUG_* bits */
-    int32_t reserved[6];       /* must be zero */
+    int32_t max_levels;        /* > 0: stop coarsening after this many matchings, the clusters
+                                  of the last one becoming the parts (as when the node target
+                                  is reached); 0 = the paper's stop rule only */
+    int32_t reserved[5];       /* must be zero */
 } hgp_options;
 
 typedef struct {

@@ -71,6 +71,7 @@ def _load():
             lib.orun_part_stats.argtypes = [vp, vp, vp]
             lib.orun_hist_row.argtypes = [vp, i32, i32, vp]
             lib.orun_score0.argtypes = [vp, i64, i64, vp, vp]
+            lib.orun_score0_nodes.argtypes = [vp, i64, i64, vp, i32, vp, vp]
             lib.oracle_match.argtypes = [i32, vp, vp, i32, vp]
             lib.oracle_gamma.argtypes = [i32, vp, vp]
             lib.oracle_gamma.restype = i32
@@ -198,6 +199,17 @@ class Run:
         rc = _load().orun_score0(self._h, int(omega), int(delta), _p(pair), _p(score))
         if rc:
             raise OracleError(rc, "score0")
+        return pair, score
+
+    def score0_nodes(self, omega, delta, nodes):
+        """Candidate and score of the listed level-0 nodes only."""
+        nodes = _i32(nodes)
+        pair = np.empty(len(nodes), dtype=np.int32)
+        score = np.empty(len(nodes), dtype=np.int32)
+        rc = _load().orun_score0_nodes(self._h, int(omega), int(delta), _p(nodes), len(nodes),
+                                       _p(pair), _p(score))
+        if rc:
+            raise OracleError(rc, "score0_nodes")
         return pair, score
 
     def refine0(self, rho, K, omega, delta):

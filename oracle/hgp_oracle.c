@@ -193,52 +193,63 @@ static int pair_valid(const olevel *g, int32_t n, int32_t m, int64_t omega, int6
     return in_n + extra <= delta;
 }
 
+/* Candidate of one node n (the steps above), with caller scratch. */
+static void score_node(const olevel *g, const int32_t *ew, int64_t omega, int64_t delta,
+                       int32_t n, int32_t *pair, int32_t *score, int64_t *hist_scratch,
+                       int32_t *touched, int32_t *stamp, ocand *cand) {
+    int32_t nt = 0;
+    for (int64_t i = g->ioff[n]; i < g->ioff[n + 1]; ++i) {
+        int32_t e = g->inc[i];
+        int64_t we = ew ? ew[e] : 1;
+        for (int64_t j = g->poff[e]; j < g->poff[e + 1]; ++j) {
+            int32_t m = g->pins[j];
+            if (m == n) continue;
+            if (hist_scratch[m] == 0) touched[nt++] = m;
+            hist_scratch[m] += we;
+        }
+    }
+    for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = n;
+    *pair = -1;
+    *score = 0;
+    int32_t best = -1;
+    for (int32_t t = 0; t < nt; ++t) {
+        int32_t m = touched[t];
+        if (best < 0 || hist_scratch[m] > hist_scratch[best] ||
+            (hist_scratch[m] == hist_scratch[best] && m > best))
+            best = m;
+    }
+    if (best >= 0 && pair_valid(g, n, best, omega, delta, stamp)) {
+        *pair = best;
+        *score = (int32_t)hist_scratch[best];
+    } else if (best >= 0) {
+        int32_t nc = 0;
+        for (int32_t t = 0; t < nt; ++t)
+            if (touched[t] != best) { cand[nc].h = hist_scratch[touched[t]]; cand[nc].m = touched[t]; nc++; }
+        qsort(cand, (size_t)nc, sizeof(ocand), cmp_cand);
+        for (int32_t c = 0; c < nc; ++c) {
+            if (pair_valid(g, n, cand[c].m, omega, delta, stamp)) {
+                *pair = cand[c].m;
+                *score = (int32_t)cand[c].h;
+                break;
+            }
+        }
+    }
+    for (int32_t t = 0; t < nt; ++t) hist_scratch[touched[t]] = 0;
+}
+
+/* nodes = NULL: every node of the level; otherwise only nodes[0..count). */
 static int score_level(const olevel *g, const int32_t *ew, int64_t omega,
                        int64_t delta, int32_t *pair, int32_t *score,
-                       int64_t *hist_scratch, int32_t *touched) {
+                       int64_t *hist_scratch, int32_t *touched,
+                       const int32_t *nodes, int32_t count) {
     int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
     ocand *cand = (ocand *)malloc(sizeof(ocand) * (size_t)g->V);
     if (!stamp || !cand) { free(stamp); free(cand); return ORC_OOM; }
     for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
-    for (int32_t n = 0; n < g->V; ++n) {
-        int32_t nt = 0;
-        for (int64_t i = g->ioff[n]; i < g->ioff[n + 1]; ++i) {
-            int32_t e = g->inc[i];
-            int64_t we = ew ? ew[e] : 1;
-            for (int64_t j = g->poff[e]; j < g->poff[e + 1]; ++j) {
-                int32_t m = g->pins[j];
-                if (m == n) continue;
-                if (hist_scratch[m] == 0) touched[nt++] = m;
-                hist_scratch[m] += we;
-            }
-        }
-        for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = n;
-        pair[n] = -1;
-        score[n] = 0;
-        int32_t best = -1;
-        for (int32_t t = 0; t < nt; ++t) {
-            int32_t m = touched[t];
-            if (best < 0 || hist_scratch[m] > hist_scratch[best] ||
-                (hist_scratch[m] == hist_scratch[best] && m > best))
-                best = m;
-        }
-        if (best >= 0 && pair_valid(g, n, best, omega, delta, stamp)) {
-            pair[n] = best;
-            score[n] = (int32_t)hist_scratch[best];
-        } else if (best >= 0) {
-            int32_t nc = 0;
-            for (int32_t t = 0; t < nt; ++t)
-                if (touched[t] != best) { cand[nc].h = hist_scratch[touched[t]]; cand[nc].m = touched[t]; nc++; }
-            qsort(cand, (size_t)nc, sizeof(ocand), cmp_cand);
-            for (int32_t c = 0; c < nc; ++c) {
-                if (pair_valid(g, n, cand[c].m, omega, delta, stamp)) {
-                    pair[n] = cand[c].m;
-                    score[n] = (int32_t)cand[c].h;
-                    break;
-                }
-            }
-        }
-        for (int32_t t = 0; t < nt; ++t) hist_scratch[touched[t]] = 0;
+    int32_t total = nodes ? count : g->V;
+    for (int32_t t = 0; t < total; ++t) {
+        int32_t n = nodes ? nodes[t] : t;
+        score_node(g, ew, omega, delta, n, pair + t, score + t, hist_scratch, touched, stamp, cand);
     }
     free(stamp); free(cand);
     return ORC_OK;
@@ -739,7 +750,7 @@ int orun_partition(orun *r, int64_t omega, int64_t delta, int32_t refine_passes)
             if (!r->pair[l] || !r->score[l] || !r->match[l] || !hist || !touched) {
                 free(hist); free(touched); rc = ORC_OOM; goto fail;
             }
-            rc = score_level(g, r->ew, omega, delta, r->pair[l], r->score[l], hist, touched);
+            rc = score_level(g, r->ew, omega, delta, r->pair[l], r->score[l], hist, touched, NULL, 0);
             free(hist); free(touched);
             if (rc) goto fail;
             rc = match_walks(V, r->pair[l], r->score[l], r->match[l]);
@@ -968,7 +979,21 @@ int orun_score0(const orun *r, int64_t omega, int64_t delta, int32_t *pair, int3
     int64_t *hist = (int64_t *)calloc((size_t)g->V, sizeof(int64_t));
     int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->V);
     if (!hist || !touched) { free(hist); free(touched); return ORC_OOM; }
-    int rc = score_level(g, r->ew, omega, delta, pair, score, hist, touched);
+    int rc = score_level(g, r->ew, omega, delta, pair, score, hist, touched, NULL, 0);
+    free(hist); free(touched);
+    return rc;
+}
+
+/* Candidate selection on level 0 for the listed nodes only (pair[t], score[t]
+ * belong to nodes[t]). */
+int orun_score0_nodes(const orun *r, int64_t omega, int64_t delta, const int32_t *nodes,
+                      int32_t count, int32_t *pair, int32_t *score) {
+    const olevel *g = &r->G[0];
+    for (int32_t t = 0; t < count; ++t) if (nodes[t] < 0 || nodes[t] >= g->V) return ORC_INVALID;
+    int64_t *hist = (int64_t *)calloc((size_t)g->V, sizeof(int64_t));
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->V);
+    if (!hist || !touched) { free(hist); free(touched); return ORC_OOM; }
+    int rc = score_level(g, r->ew, omega, delta, pair, score, hist, touched, nodes, count);
     free(hist); free(touched);
     return rc;
 }

@@ -252,10 +252,13 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
     int32_t passes = 1;
     uint32_t debug = 0;
+    int32_t max_levels = 0;
     if (opt) {
         if (opt->refine_passes < 0) return fail(g, HGP_ERR_INVALID_ARG, "refine_passes must be >= 0");
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 5; ++i)
             if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->max_levels < 0) return fail(g, HGP_ERR_INVALID_ARG, "max_levels must be >= 0");
+        max_levels = opt->max_levels;
         if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
                                      HGP_DEBUG_NO_BITMAP | HGP_DEBUG_FORCE_CLUSTER))
             return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
@@ -346,7 +349,8 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
                 break;
             }
             if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_GAMMA, l, L.gamma, L.V, s);
-            if ((int64_t)V2 <= target) {   // coarsest clusters become the parts
+            if ((int64_t)V2 <= target ||              // coarsest clusters become the parts
+                (max_levels > 0 && (int)levels.size() >= max_levels)) {
                 K = V2;
                 top_gamma = true;
                 break;

@@ -40,7 +40,7 @@ class HgpError(RuntimeError):
 
 class hgp_options(ctypes.Structure):
     _fields_ = [("refine_passes", ctypes.c_int32), ("debug", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class hgp_result(ctypes.Structure):
@@ -157,11 +157,11 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
 
 
 def hgp_partition(handle, omega, delta, part_ids, part_weight=None, part_inbound=None,
-                  refine_passes=1, debug=0):
+                  refine_passes=1, debug=0, max_levels=0):
     """hgp_partition into caller buffers (host numpy or device torch tensors).
     Returns (cost, num_parts, num_levels)."""
     lib = load()
-    opt = hgp_options(refine_passes, debug)
+    opt = hgp_options(refine_passes, debug, max_levels)
     res = hgp_result()
     res.part_ids = _ptr(part_ids)
     res.part_weight = _ptr(part_weight)
@@ -222,11 +222,12 @@ class Graph:
     def from_hypergraph(cls, g, stream=None):
         return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream)
 
-    def partition(self, omega, delta, refine_passes=1, debug=0) -> Result:
+    def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)
         pw = np.empty(self.num_nodes, dtype=np.int64)
         pin = np.empty(self.num_nodes, dtype=np.int32)
-        cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug)
+        cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug,
+                                          max_levels)
         return Result(ids, cost, npart, nlev, pw[:npart], pin[:npart])
 
     def partition_device(self, omega, delta, part_ids, part_weight=None, part_inbound=None,

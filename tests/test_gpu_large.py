@@ -1,0 +1,92 @@
+"""Full-size first-level parity for the two largest workloads (262,144-node
+random SNN, 67M pins; 204,800-node layered conv-style SNN, ~1.4e8 pins).
+
+A whole partition of these takes hundreds of coarsening levels and far more
+oracle time than a test can spend, so the test runs the first matching only
+(max_levels = 1, no refinement) at full size, in the scoring kernel's
+large-level configuration (the 8-CTA distributed shared-memory histogram),
+and checks:
+  - candidate and score of 512 seeded sampled nodes against the oracle,
+    which computes them one node at a time (Eq. 2, Sec. III-B.2);
+  - the matching properties of Sec. III-A / III-B.3 on every node;
+  - the returned partition recounted independently (Eq. 1 cost, node
+    weights, distinct inbound hyperedges, both bounds).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+hgp = pytest.importorskip("paper_2604_14411_gb300")
+from paper_2604_14411_gb300 import hgp as H  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def recount(g, part_ids):
+    """(cost, part weights, part inbound counts) with vectorised numpy."""
+    off = g.offsets.astype(np.int64)
+    E = len(off) - 1
+    sizes = np.diff(off)
+    eid = np.repeat(np.arange(E, dtype=np.int64), sizes)
+    parts = part_ids[g.pins].astype(np.int64)
+    K = int(part_ids.max()) + 1
+    key = np.unique(eid * K + parts)
+    lam = np.bincount(key // K, minlength=E)
+    cost = int((lam - 1).sum())
+    weight = np.bincount(part_ids, minlength=K)
+    first = np.zeros(len(g.pins), bool)
+    first[off[:-1]] = True
+    ink = np.unique(parts[~first] * E + eid[~first])
+    inbound = np.bincount(ink // E, minlength=K)
+    return cost, weight, inbound
+
+
+def check_matching(pair, match):
+    V = len(pair)
+    idx = np.arange(V)
+    assert np.array_equal(match[match], idx)                       # involution
+    m = match != idx
+    assert np.all((pair[m] == match[m]) | (pair[match[m]] == idx[m]))   # pairing edges only
+    has = pair >= 0
+    root = has & (pair[np.where(has, pair, 0)] == idx)
+    assert np.all(match[root] == pair[root])                       # two-cycles matched
+    free = has & ~m
+    assert np.all(match[pair[free]] != pair[free])                 # a free node's candidate is taken
+
+
+@pytest.mark.parametrize("name,make,omega,delta", [
+    ("snn256k", lambda: synth.snn_256k(0), 1 << 10, 1 << 12),
+    ("conv200k", lambda: synth.conv_200k(0), 1 << 12, 1 << 16),
+])
+def test_first_level_full_size(name, make, omega, delta):
+    g = make()
+    with hgp.Graph.from_hypergraph(g) as G:
+        res = G.partition(omega, delta, refine_passes=0, max_levels=1,
+                          debug=H.HGP_DEBUG_KEEP_LEVELS)
+        pair = G.level_array(0, H.HGP_LEVEL_PAIR)
+        score = G.level_array(0, H.HGP_LEVEL_SCORE)
+        match = G.level_array(0, H.HGP_LEVEL_MATCH)
+    assert res.num_levels == 1
+    rng = np.random.default_rng(1234)
+    nodes = np.sort(rng.choice(g.num_nodes, size=512, replace=False)).astype(np.int32)
+    with oracle.Run.from_graph(g) as r:
+        op, osc = r.score0_nodes(omega, delta, nodes)
+    assert np.array_equal(pair[nodes], op), name
+    assert np.array_equal(score[nodes], osc), name
+    check_matching(pair, match)
+    cost, weight, inbound = recount(g, res.part_ids)
+    assert cost == res.cost
+    assert np.array_equal(weight[:res.num_parts], res.part_weight)
+    assert np.array_equal(inbound[:res.num_parts], res.part_inbound)
+    assert weight.max() <= omega and inbound.max() <= delta
+    assert res.num_parts == g.num_nodes - int((match != np.arange(g.num_nodes)).sum()) // 2

@@ -127,6 +127,15 @@ def test_pair_is_first_valid_in_hist_order(seed):
             assert pair[pair[x]] == x
 
 
+def test_score_of_sampled_nodes_matches_full_scoring():
+    g = synth.random_snn(600, 12, 2)
+    r = oracle.Run.from_graph(g)
+    pair, score = r.score0(10, 60)
+    nodes = np.array([5, 0, 599, 77, 300, 77], np.int32)
+    p2, s2 = r.score0_nodes(10, 60, nodes)
+    assert np.array_equal(p2, pair[nodes]) and np.array_equal(s2, score[nodes])
+
+
 # ---------------------------------------------------------------- matching
 def _check_matching(pair, score, match):
     V = len(pair)
