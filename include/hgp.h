@@ -131,6 +131,22 @@ typedef struct {
 int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta,
                   const hgp_options *opt, hgp_result *res);
 
+/*
+ * Partition `count` handles at once (the batched workload of many uneven
+ * hypergraphs).  Instance i uses bounds omegas[i], deltas[i] and writes
+ * res[i] exactly as hgp_partition(gs[i], omegas[i], deltas[i], opt, &res[i])
+ * would (same options for all).  Worker threads (up to 16) run instances
+ * concurrently, each on a CUDA stream of its own created for the call, so
+ * the per-level kernels and host round trips of different instances overlap
+ * on the device.  Handles must be distinct; their own streams are waited on
+ * first.  status (optional, [count]) receives every instance's status; the
+ * return value is the first non-OK status in index order, or HGP_OK.
+ * Device outputs (HGP_OUTPUT_DEVICE) are complete when the call returns.
+ */
+int hgp_partition_batch(hgp_graph *const *gs, int32_t count, const int64_t *omegas,
+                        const int64_t *deltas, const hgp_options *opt, hgp_result *res,
+                        int32_t *status);
+
 #define HGP_MAX_STAT_LEVELS 4096
 typedef struct {
     int32_t num_levels;        /* levels of the last hgp_partition */

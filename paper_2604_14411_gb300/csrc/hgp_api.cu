@@ -1,8 +1,10 @@
 // C ABI of the library (include/hgp.h): handle lifetime, the level loop of
 // Sec. II-B (coarsen until ceil(W / Omega) nodes or no merge, then refine
 // from the coarsest level down while projecting), and result delivery.
+#include <atomic>
 #include <chrono>
 #include <cstring>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -245,8 +247,10 @@ void keep_array(hgp_graph *g, int which, int level, const int32_t *d, int64_t n,
 }
 }  // namespace
 
-extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const hgp_options *opt,
-                             hgp_result *res) {
+// hgp_partition on an explicit stream (the batch entry point runs several
+// handles concurrently, each on a stream of its own).
+static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_options *opt,
+                        hgp_result *res, cudaStream_t s) {
     if (!g || !res) return HGP_ERR_INVALID_ARG;
     if (omega < 1 || delta < 0) return fail(g, HGP_ERR_INVALID_ARG, "omega must be >= 1 and delta >= 0");
     if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
@@ -269,7 +273,6 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
         return fail(g, HGP_ERR_INFEASIBLE, "a single node exceeds omega or delta; no partition exists");
     double t0 = now_ms();
     int64_t launches0 = g_launches;
-    cudaStream_t s = g->stream;
     Arena lv, tmp;
     lv.stream = s;
     tmp.stream = s;
@@ -487,6 +490,55 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     st.ms_partition = now_ms() - t0;
     return HGP_OK;
 #undef CKP
+}
+
+extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const hgp_options *opt,
+                             hgp_result *res) {
+    if (!g) return HGP_ERR_INVALID_ARG;
+    return partition_on(g, omega, delta, opt, res, g->stream);
+}
+
+// Many handles at once: worker threads take instances from a shared counter
+// and run each on a stream of their own, so the small per-level kernels and
+// host round trips of different instances overlap on the GPU.  Every
+// instance's result is exactly its hgp_partition result.
+extern "C" int hgp_partition_batch(hgp_graph *const *gs, int32_t count, const int64_t *omegas,
+                                   const int64_t *deltas, const hgp_options *opt,
+                                   hgp_result *res, int32_t *status) {
+    if (count < 0 || (count > 0 && (!gs || !omegas || !deltas || !res))) return HGP_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (!gs[i]) return HGP_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HGP_ERR_CUDA;
+    int workers = count < 16 ? count : 16;
+    std::atomic<int32_t> next(0);
+    std::vector<int> rc(count > 0 ? count : 1, HGP_OK);
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+        for (;;) {
+            int32_t i = next.fetch_add(1);
+            if (i >= count) break;
+            if (!s) { rc[i] = HGP_ERR_CUDA; continue; }
+            cudaStreamSynchronize(gs[i]->stream);      // the handle's own work is done
+            rc[i] = partition_on(gs[i], omegas[i], deltas[i], opt, &res[i], s);
+        }
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+    if (workers > 0) work();
+    for (auto &t : pool) t.join();
+    int first = HGP_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        if (status) status[i] = rc[i];
+        if (first == HGP_OK && rc[i] != HGP_OK) first = rc[i];
+    }
+    return first;
 }
 
 extern "C" int hgp_get_stats(const hgp_graph *g, hgp_stats *st) {

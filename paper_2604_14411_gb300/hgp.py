@@ -69,7 +69,7 @@ class hgp_stats(ctypes.Structure):
 # every symbol declared in include/hgp.h
 EXPORTS = ("hgp_create", "hgp_partition", "hgp_get_stats", "hgp_get_level_len",
            "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy",
-           "hgp_score_noalloc")
+           "hgp_score_noalloc", "hgp_partition_batch")
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.hgp_destroy.argtypes = [vp]
     lib.hgp_destroy.restype = None
     lib.hgp_score_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i64, i64, vp, vp, vp]
+    lib.hgp_partition_batch.argtypes = [vp, i32, vp, vp, ctypes.POINTER(hgp_options), vp, vp]
+    lib.hgp_partition_batch.restype = ctypes.c_int
     lib.hgp_score_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -199,6 +201,36 @@ def hgp_last_error(handle) -> str:
 def hgp_destroy(handle):
     if handle:
         load().hgp_destroy(handle)
+
+
+def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_levels=0):
+    """Partitions several Graph objects concurrently; returns a list of Result."""
+    lib = load()
+    n = len(graphs)
+    handles = (ctypes.c_void_p * n)(*[g._h.value for g in graphs])
+    om = np.ascontiguousarray(omegas, dtype=np.int64)
+    de = np.ascontiguousarray(deltas, dtype=np.int64)
+    res = (hgp_result * n)()
+    bufs = []
+    for i, g in enumerate(graphs):
+        ids = np.empty(g.num_nodes, dtype=np.int32)
+        pw = np.empty(g.num_nodes, dtype=np.int64)
+        pin = np.empty(g.num_nodes, dtype=np.int32)
+        bufs.append((ids, pw, pin))
+        res[i].part_ids, res[i].part_weight, res[i].part_inbound = ids.ctypes.data, pw.ctypes.data, pin.ctypes.data
+        res[i].out_flags = 0
+    status = np.zeros(max(n, 1), dtype=np.int32)
+    opt = hgp_options(refine_passes, debug, max_levels)
+    rc = lib.hgp_partition_batch(handles, n, om.ctypes.data, de.ctypes.data, ctypes.byref(opt),
+                                 ctypes.addressof(res), status.ctypes.data)
+    if rc != HGP_OK:
+        bad = int(np.nonzero(status[:n])[0][0])
+        raise HgpError(rc, f"instance {bad}: " + lib.hgp_last_error(graphs[bad]._h).decode())
+    out = []
+    for i, (ids, pw, pin) in enumerate(bufs):
+        k = res[i].num_parts
+        out.append(Result(ids, int(res[i].cost), int(k), int(res[i].num_levels), pw[:k], pin[:k]))
+    return out
 
 
 @dataclass

@@ -1,0 +1,79 @@
+"""hgp_partition_batch: many uneven hypergraphs partitioned concurrently
+(each on its own stream); every instance must equal the oracle bit-exactly,
+and a failing instance must not disturb the others."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+hgp = pytest.importorskip("paper_2604_14411_gb300")
+from paper_2604_14411_gb300 import hgp as H  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _instances():
+    out = []
+    for i in range(12):
+        if i % 3 == 2:
+            g = synth.conv_snn(4, 6, 4 + i % 4, 3, 4 + i % 4, 100 + i)
+            om, de = 32, 300
+        else:
+            g = synth.random_snn(300 + 173 * i, 6 + i, 100 + i, size_max=10 + 2 * i)
+            om, de = 24 + 2 * i, 60 + 10 * i
+        out.append((g, om, de))
+    return out
+
+
+def test_batch_matches_oracle_per_instance():
+    inst = _instances()
+    graphs = [hgp.Graph.from_hypergraph(g) for g, _, _ in inst]
+    try:
+        got = H.hgp_partition_batch(graphs, [o for _, o, _ in inst], [d for _, _, d in inst])
+    finally:
+        for G in graphs:
+            G.close()
+    for (g, om, de), r in zip(inst, got):
+        want = oracle.partition(g, om, de)
+        assert np.array_equal(r.part_ids, want.part_ids)
+        assert r.cost == want.cost and r.num_parts == want.num_parts
+        assert np.array_equal(r.part_weight, want.part_weight)
+        assert np.array_equal(r.part_inbound, want.part_inbound)
+
+
+def test_batch_reports_per_instance_status():
+    inst = _instances()[:4]
+    graphs = [hgp.Graph.from_hypergraph(g) for g, _, _ in inst]
+    lib = H.load()
+    import ctypes
+    n = len(graphs)
+    handles = (ctypes.c_void_p * n)(*[G._h.value for G in graphs])
+    om = np.array([o for _, o, _ in inst], np.int64)
+    de = np.array([d for _, _, d in inst], np.int64)
+    de[1] = 0                                    # instance 1 is infeasible
+    res = (H.hgp_result * n)()
+    keep = []
+    for i, G in enumerate(graphs):
+        ids = np.empty(G.num_nodes, np.int32)
+        keep.append(ids)
+        res[i].part_ids = ids.ctypes.data
+    status = np.full(n, -1, np.int32)
+    rc = lib.hgp_partition_batch(handles, n, om.ctypes.data, de.ctypes.data, None,
+                                 ctypes.addressof(res), status.ctypes.data)
+    assert rc == H.HGP_ERR_INFEASIBLE
+    assert status.tolist() == [0, H.HGP_ERR_INFEASIBLE, 0, 0]
+    for i in (0, 2, 3):
+        g, o, d = inst[i]
+        want = oracle.partition(g, o, d)
+        assert np.array_equal(keep[i], want.part_ids) and res[i].cost == want.cost
+    for G in graphs:
+        G.close()
