@@ -83,6 +83,16 @@ extern thread_local int64_t g_launches;
 inline void count_launch() { ++g_launches; }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Raises a kernel's dynamic shared-memory limit to the device maximum, once
+// per (device, kernel) under a lock.  The limit is process-wide state, so
+// setting it per launch from several host threads (hgp_partition_batch)
+// could lower it between another thread's set and launch.
+cudaError_t allow_dynamic_smem_ptr(const void *kernel);
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kernel) {
+    return allow_dynamic_smem_ptr(reinterpret_cast<const void *>(kernel));
+}
 int num_sms();
 
 // ---------------- primitives (k_prims.cu) ----------------

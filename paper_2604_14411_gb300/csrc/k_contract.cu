@@ -270,8 +270,8 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     k_union_count<<<grid1d(V2), 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.noff, cntI, cntN, dmax,
                                              mlist, dmax + 1);
     count_launch();
-    e = cudaFuncSetAttribute(k_union_merged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-    if (!e) e = cudaFuncSetAttribute(k_union_merged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    e = allow_dynamic_smem(k_union_merged<false>);
+    if (!e) e = allow_dynamic_smem(k_union_merged<true>);
     if (e) return e;
     k_union_merged<false><<<mblocks, 256, ssm, s>>>(mlist, dmax + 1, rep_of, L.match, L.ioff, L.inc,
                                                     L.noff, L.inn, cntI, cntN, dmax, nullptr, nullptr,

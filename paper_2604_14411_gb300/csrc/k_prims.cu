@@ -2,9 +2,33 @@
 // These are the prefix-sum and sort building blocks of the level-0 incidence
 // build (Sec. II-C) and of refinement (Sec. IV-B): all integer, all stable,
 // so every result is deterministic.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "hgp_internal.cuh"
 
 namespace hgp {
+
+cudaError_t allow_dynamic_smem_ptr(const void *kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, kernel})) return cudaSuccess;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e) return e;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (!e) done.insert({dev, kernel});
+    return e;
+}
 
 thread_local int64_t g_launches = 0;
 

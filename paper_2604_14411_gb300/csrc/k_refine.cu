@@ -190,6 +190,10 @@ static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, in
         size_t smem = use_smem ? sizeof(int32_t) * (size_t)K : 0;
         int blocks = grid_warps(L.E);
         if (use_smem && blocks > num_sms() * 4) blocks = num_sms() * 4;   // fewer flushes
+        if (use_smem) {
+            cudaError_t ea = allow_dynamic_smem(k_runs);
+            if (ea) return ea;
+        }
         k_runs<<<blocks, 256, smem, s>>>(L.E, L.poff, pv, L.src, L.sdst, rho, R.rpart, R.rcnt,
                                          R.rcin, rpos, R.nrun, inb, K, use_smem);
         count_launch();
@@ -644,7 +648,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
         size_t smem = 2 * sizeof(int32_t) * (size_t)K;
-        e = cudaFuncSetAttribute(k_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dynamic_smem(k_propose<true>);
         if (e) return e;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true>, kPropThreads, smem);

@@ -51,8 +51,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
                  !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER));
     int sms = num_sms();
     if (dense) {
-        e = cudaFuncSetAttribute(k_score<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dense_smem);
+        e = allow_dynamic_smem(k_score<true>);
         if (e) return e;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, dense_smem);
@@ -84,7 +83,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     while (gcap < 2 * distinct) gcap <<= 1;
     if (gcap > (1ull << 30)) return cudaErrorMemoryAllocation;
     a.gcap = (int32_t)gcap;
-    e = cudaFuncSetAttribute(k_score<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_bytes);
+    e = allow_dynamic_smem(k_score<false>);
     if (e) return e;
     int blocks = sms * 2;
     if (blocks > L.V) blocks = L.V;

@@ -146,8 +146,7 @@ bool launch_score_cluster(const ScoreArgs &a, int max_smem, cudaStream_t s, cuda
     int32_t slice = (a.V + kClusterCtas - 1) / kClusterCtas;
     size_t smem = sizeof(uint32_t) * (size_t)a.bm_words + sizeof(int32_t) * (size_t)slice;
     if (smem + 4096 > (size_t)max_smem) return false;
-    cudaError_t e = cudaFuncSetAttribute(k_score_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_score_cluster);
     if (e) { *err = e; return true; }
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kScoreThreads);

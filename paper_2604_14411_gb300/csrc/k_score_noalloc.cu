@@ -99,8 +99,7 @@ extern "C" int hgp_score_noalloc(int32_t num_nodes, int32_t num_edges, const int
     // dense shared-memory histogram only (no global tables)
     size_t smem = sizeof(uint32_t) * (size_t)a.bm_words + sizeof(int32_t) * (size_t)num_nodes;
     if (smem + 2048 > (size_t)max_smem) return HGP_ERR_SCRATCH_LIMIT;
-    if (cudaFuncSetAttribute(k_score<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (allow_dynamic_smem(k_score<true>) != cudaSuccess)
         return HGP_ERR_CUDA;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, smem);
