@@ -25,7 +25,7 @@ int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, co
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            PropTiming *pt, cudaStream_t s);
+                            PropTiming *pt, const PropReuse &ru, cudaStream_t s);
 void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
                  cudaStream_t s);
 cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
@@ -388,12 +388,30 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     CKP(cudaMemsetAsync(d_rstat, 0, sizeof(long long) * 3 * levels.size(), s), "memset");
     CKP(cudaMemsetAsync(d_applied, 0, sizeof(unsigned long long), s), "memset");
     tm.start(3, &ev_a);
+    // proposal buffers, alternating between levels so the coarser level's stay readable
+    int32_t *pbuf[2][2];
+    int32_t *d_flag = nullptr;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) CKP(dalloc(lv, &pbuf[i][j], g->L0.V), "alloc");
+    CKP(dalloc(lv, &d_flag, 1), "alloc");
+    CKP(cudaMemsetAsync(d_flag, 0, sizeof(int32_t), s), "memset");
     for (int l = L; l >= 0; --l) {
         const Level &Lv = levels[l];
         if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
         for (int p = 0; p < passes; ++p) {
+            PropReuse ru;
+            int cur = l & 1;
+            ru.out_gain = pbuf[cur][0];
+            ru.out_pd = pbuf[cur][1];
+            ru.applied_flag = d_flag;
+            if (p == 0 && l < L && passes > 0) {      // the coarser level's last pass is available
+                ru.prev_gain = pbuf[cur ^ 1][0];
+                ru.prev_pd = pbuf[cur ^ 1][1];
+                ru.gamma = Lv.gamma;
+                ru.match = Lv.match;
+            }
             CKP(run_refine_pass(tmp, Lv, g->ew, g->wsum_e, rho, K, omega, delta, d_rstat + 3 * l,
-                                d_applied, debug, tm.on ? &ptime : nullptr, s), "refine");
+                                d_applied, debug, tm.on ? &ptime : nullptr, ru, s), "refine");
             tmp.reset();
         }
         if (debug & HGP_DEBUG_KEEP_LEVELS) {

@@ -78,6 +78,14 @@ struct PropTiming {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 
+// Proposal buffers carried from one refinement pass to the next finer level.
+struct PropReuse {
+    int32_t *out_gain = nullptr, *out_pd = nullptr;          // this pass's proposals [V]
+    const int32_t *prev_gain = nullptr, *prev_pd = nullptr;  // coarser level's, or null
+    const int32_t *gamma = nullptr, *match = nullptr;        // this level's gamma / match
+    int32_t *applied_flag = nullptr;   // device: in = coarser pass applied moves; out = this pass
+};
+
 // ---------------- launch bookkeeping ----------------
 extern thread_local int64_t g_launches;
 inline void count_launch() { ++g_launches; }

@@ -211,6 +211,13 @@ struct PropArgs {
     int32_t *gpres;     // per-CTA global tables when K is large
     int32_t *next;      // work counter: nodes are taken dynamically
     unsigned long long *bytes;   // algorithmic bytes (timing runs only)
+    // Reuse of the previous (one level coarser) pass's proposals: when that pass
+    // applied no move, a node that was not split by the last matching keeps
+    // exactly its coarse node's proposal (part presence on its hyperedges, part
+    // sizes and its own savings are unchanged by splitting a pair inside one part).
+    const int32_t *prev_gain, *prev_pd;   // proposals of the coarser level (null = none)
+    const int32_t *gamma, *match;         // this level's map to the coarser level
+    const int32_t *prev_applied;          // device flag: the coarser pass applied moves
 };
 
 template <bool DENSE>
@@ -231,6 +238,15 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         __syncthreads();
         const int32_t n = s_n;
         if (n >= a.V) break;
+        if (a.prev_gain && *a.prev_applied == 0 && a.match[n] == n) {
+            if (threadIdx.x == 0) {
+                int32_t c = a.gamma[n];
+                a.gain[n] = a.prev_gain[c];
+                a.pd[n] = a.prev_pd[c];
+            }
+            __syncthreads();
+            continue;
+        }
         int32_t ps = a.rho[n];
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
         long long sav = 0, wI = 0;
@@ -547,7 +563,7 @@ __global__ void k_gseq_i64(int32_t M, const int32_t *gseq, const int32_t *vdelta
 // single CTA: k* = argmax over valid prefixes of (G, length); apply iff G > 0.
 // stats[0..2] = (M, k*, gain); *applied accumulates k* over passes.
 __global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32_t *kstar,
-                         long long *stats, unsigned long long *applied) {
+                         long long *stats, unsigned long long *applied, int32_t *applied_flag) {
     __shared__ long long bg[1024];
     __shared__ int32_t bk[1024];
     long long g = 0;
@@ -577,6 +593,7 @@ __global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32
         *kstar = apply ? bk[0] : 0;
         if (stats) { stats[0] = M; stats[1] = apply ? bk[0] : 0; stats[2] = apply ? bg[0] : 0; }
         if (applied && apply) atomicAdd(applied, (unsigned long long)bk[0]);
+        if (applied_flag) *applied_flag = apply ? 1 : 0;
     }
 }
 
@@ -613,7 +630,7 @@ __global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            PropTiming *pt, cudaStream_t s) {
+                            PropTiming *pt, const PropReuse &ru, cudaStream_t s) {
     int32_t V = L.V;
     int32_t *size, *inb;
     cudaError_t e = dalloc(tmp, &size, K);
@@ -627,14 +644,13 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     e = build_runs(tmp, L, rho, K, R, inb, s);
     if (e) return e;
     // proposals
-    int32_t *pg, *ppd;
-    e = dalloc(tmp, &pg, V);
-    if (!e) e = dalloc(tmp, &ppd, V);
-    if (e) return e;
+    int32_t *pg = ru.out_gain, *ppd = ru.out_pd;     // kept for the next finer level
     PropArgs pa{};
     pa.V = V; pa.K = K; pa.w = L.w; pa.ioff = L.ioff; pa.inc = L.inc; pa.poff = L.poff;
     pa.ew = ew; pa.rho = rho; pa.size = size; pa.rpart = R.rpart; pa.rcnt = R.rcnt;
     pa.nrun = R.nrun; pa.omega = omega; pa.gain = pg; pa.pd = ppd;
+    pa.prev_gain = ru.prev_gain; pa.prev_pd = ru.prev_pd;
+    pa.gamma = ru.gamma; pa.match = ru.match; pa.prev_applied = ru.applied_flag;
     e = dalloc(tmp, &pa.next, 1);
     if (!e) e = cudaMemsetAsync(pa.next, 0, sizeof(int32_t), s);
     if (e) return e;
@@ -682,7 +698,11 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     e = cudaMemcpyAsync(&M, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return e;
-    if (M == 0) return cudaMemsetAsync(d_stats, 0, 3 * sizeof(long long), s);
+    if (M == 0) {
+        e = cudaMemsetAsync(d_stats, 0, 3 * sizeof(long long), s);
+        if (!e) e = cudaMemsetAsync(ru.applied_flag, 0, sizeof(int32_t), s);
+        return e;
+    }
     uint32_t *mkey, *mkey2;
     int32_t *mnode, *mv_n, *mv_ps, *mv_pd, *idx_of, *gseq, *lose, *gin;
     e = dalloc(tmp, &mkey, M);
@@ -823,7 +843,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     int32_t *dk;
     e = dalloc(tmp, &dk, 1);
     if (e) return e;
-    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, d_stats, d_applied);
+    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, d_stats, d_applied, ru.applied_flag);
     count_launch();
     k_apply<<<grid1d(M), 256, 0, s>>>(M, dk, mv_n, mv_pd, rho);
     count_launch();
