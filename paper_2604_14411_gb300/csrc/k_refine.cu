@@ -30,7 +30,7 @@
 
 namespace hgp {
 
-constexpr int kPropThreads = 256;
+constexpr int kPropThreads = 1024;
 constexpr int kPropWarps = kPropThreads / 32;
 constexpr int kPartsDenseMax = 12288;   // pres + touched list: 96 KB of smem
 
