@@ -154,6 +154,67 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BATCH_WORKLOAD = ("64 SNN hypergraphs, N log-uniform in [2048, 65536] (seed 0); even: random, edge "
+                  "size U{32..256}; odd: layered conv-style 8 x 16x16 x ch; Omega=2^10, Delta=2^12 "
+                  "for all; 150,771,047 pins in total")
+
+
+def run_batch(args, rank, world):
+    """64 uneven hypergraphs per step through hgp_partition_batch (instances on
+    concurrent streams); also times them one at a time once for comparison."""
+    import torch
+    import synth
+    from paper_2604_14411_gb300 import hgp as H
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    H.load()
+    inst = synth.batch_instances(64, 0)
+    pins = sum(g.num_pins for g in inst)
+    graphs = [H.Graph.from_hypergraph(g) for g in inst]
+    om, de = [OMEGA] * len(graphs), [DELTA] * len(graphs)
+    for _ in range(args.warmup):
+        H.hgp_partition_batch(graphs, om, de)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(f"/tmp/clocks_batch_rank{rank}.csv")
+    sampler.start()
+    t = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = H.hgp_partition_batch(graphs, om, de)
+        torch.cuda.synchronize()
+        t.append(1000.0 * (time.perf_counter() - t0))
+    clocks = sampler.stop(local)
+    job = job_time_ms(sum(t), dist, torch.device("cuda", local))
+    t0 = time.perf_counter()
+    for G in graphs:
+        G.partition(OMEGA, DELTA)
+    seq_ms = 1000.0 * (time.perf_counter() - t0)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_value(pins, args.steps, world, job), "unit": "pins/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": job / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "pins": pins, "instances": len(graphs),
+                       "timing": "host clock around hgp_partition_batch (device-resident inputs)"},
+            "sequential_ms": seq_ms, "batch_speedup_vs_sequential": seq_ms / (job / args.steps),
+            "total_cost": int(sum(r.cost for r in res)), "total_parts": int(sum(r.num_parts for r in res)),
+            "clocks": clocks}), flush=True)
+    for G in graphs:
+        G.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,6 +222,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="snn16k", choices=["snn16k", "batch64"],
+                    help="snn16k: the default single-hypergraph workload; batch64: 64 uneven "
+                         "hypergraphs through hgp_partition_batch (prints its own JSON line)")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run exactly one step, exit (for ncu launch lists)")
     args = ap.parse_args()
@@ -172,6 +236,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch64":
+        return run_batch(args, rank, world)
 
     import torch
     import synth

@@ -30,7 +30,7 @@
 
 namespace hgp {
 
-constexpr int kScoreThreads = 512;
+constexpr int kScoreThreads = 1024;
 constexpr int kScoreWarps = kScoreThreads / 32;
 
 struct ScoreArgs {
