@@ -32,15 +32,20 @@ cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const in
                          int32_t K, int32_t *part_ids, int64_t *pw, int32_t *pin,
                          unsigned long long *d_cost, int32_t *d_nparts, cudaStream_t s);
 
-__global__ void k_node_maxima(int32_t N, const int32_t *w, const int32_t *noff, int32_t *out) {
-    int32_t mw = 0, mi = 0;
+__global__ void k_node_maxima(int32_t N, const int32_t *w, const int32_t *noff, int32_t E,
+                              const int32_t *poff, int32_t *out) {
+    int32_t mw = 0, mi = 0, me = 0;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (int64_t)gridDim.x * blockDim.x) {
         mw = max(mw, w[n]);
         mi = max(mi, noff[n + 1] - noff[n]);
     }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x)
+        me = max(me, poff[e + 1] - poff[e]);
     atomicMax(&out[0], mw);
     atomicMax(&out[1], mi);
+    atomicMax(&out[2], me);
 }
 
 __global__ void k_fill_one(int32_t *p, int64_t n) {
@@ -172,11 +177,11 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     }
     // node maxima and total weight for the singleton check and the stop rule
     int32_t *mx = nullptr;
-    CKC(dalloc(tmp, &mx, 2), "alloc");
-    CKC(cudaMemsetAsync(mx, 0, sizeof(int32_t) * 2, s), "memset");
-    k_node_maxima<<<num_sms() * 4, 256, 0, s>>>(num_nodes, L.w, L.noff, mx);
+    CKC(dalloc(tmp, &mx, 3), "alloc");
+    CKC(cudaMemsetAsync(mx, 0, sizeof(int32_t) * 3, s), "memset");
+    k_node_maxima<<<num_sms() * 4, 256, 0, s>>>(num_nodes, L.w, L.noff, num_edges, L.poff, mx);
     count_launch();
-    int32_t hmx[2];
+    int32_t hmx[3];
     CKC(cudaMemcpyAsync(hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s), "read maxima");
     std::vector<int32_t> hw;
     if (node_weights) {
@@ -189,6 +194,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     g->max_w = hmx[0];
     g->max_in = hmx[1];
     L.max_in = hmx[1];
+    L.max_edge = hmx[2];
     int64_t W = 0;
     if (node_weights) for (int32_t x : hw) W += x;
     else W = num_nodes;

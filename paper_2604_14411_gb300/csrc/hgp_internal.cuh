@@ -30,6 +30,7 @@ struct Level {
     int32_t V = 0, E = 0;
     int64_t P = 0, Q = 0;
     int32_t max_in = 0;         // largest |in(n)| of the level
+    int32_t max_edge = 0;       // largest |pins(e)| of the level
     int32_t *w = nullptr;
     int32_t *poff = nullptr, *pins = nullptr;
     int32_t *ioff = nullptr, *inc = nullptr;

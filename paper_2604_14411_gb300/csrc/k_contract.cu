@@ -163,7 +163,7 @@ template <bool WRITE>
 __global__ void k_coarse_pins(int32_t E, const int32_t *poff, const int32_t *pins,
                               const int32_t *match, const int32_t *gamma, const int32_t *ioff,
                               const int32_t *inc, int32_t *cnt, const int32_t *poff2,
-                              int32_t *pins2) {
+                              int32_t *pins2, int32_t *max_edge) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned lt = (1u << lane_id()) - 1u;
@@ -183,7 +183,7 @@ __global__ void k_coarse_pins(int32_t E, const int32_t *poff, const int32_t *pin
             if (WRITE && k) pins2[outpos + kept + __popc(ball & lt)] = gamma[m];
             kept += __popc(ball);
         }
-        if (!WRITE && lane_id() == 0) cnt[e] = kept;
+        if (!WRITE && lane_id() == 0) { cnt[e] = kept; atomicMax(max_edge, kept); }
     }
 }
 
@@ -241,8 +241,8 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     int32_t *mlist = nullptr;
     e = dalloc(tmp, &rep_of, V2);
     if (!e) e = dalloc(tmp, &mlist, V2);
-    if (!e) e = dalloc(tmp, &dmax, 2);          // [0] largest |in'|, [1] matched pairs queued
-    if (!e) e = cudaMemsetAsync(dmax, 0, 2 * sizeof(int32_t), s);
+    if (!e) e = dalloc(tmp, &dmax, 3);    // [0] largest |in'|, [1] pairs queued, [2] largest |e'|
+    if (!e) e = cudaMemsetAsync(dmax, 0, 3 * sizeof(int32_t), s);
     if (!e) e = dalloc(tmp, &cntI, V2);
     if (!e) e = dalloc(tmp, &cntN, V2);
     if (!e) e = dalloc(tmp, &cntP, L.E);
@@ -278,14 +278,16 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
                                                     nullptr, nullptr, cap);
     count_launch();
     k_coarse_pins<false><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
-                                                         L.ioff, L.inc, cntP, nullptr, nullptr);
+                                                         L.ioff, L.inc, cntP, nullptr, nullptr,
+                                                         dmax + 2);
     count_launch();
     e = counts_to_offsets(tmp, cntI, H.ioff, V2, s);
     if (!e) e = counts_to_offsets(tmp, cntN, H.noff, V2, s);
     if (!e) e = counts_to_offsets(tmp, cntP, H.poff, L.E, s);
     if (e) return e;
-    int32_t tot[4];
+    int32_t tot[5];
     e = cudaMemcpyAsync(&tot[3], dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&tot[4], dmax + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[0], H.ioff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[1], H.noff + V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[2], H.poff + L.E, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -295,6 +297,7 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     H.P = tot[0];
     H.Q = tot[1];
     H.max_in = tot[3];
+    H.max_edge = tot[4];
     e = dalloc(keep, &H.inc, H.P);
     if (!e) e = dalloc(keep, &H.inn, H.Q);
     if (!e) e = dalloc(keep, &H.pins, H.P);
@@ -310,7 +313,8 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     }
     count_launch();
     k_coarse_pins<true><<<grid_warps(L.E), 256, 0, s>>>(L.E, L.poff, L.pins, L.match, L.gamma,
-                                                        L.ioff, L.inc, nullptr, H.poff, H.pins);
+                                                        L.ioff, L.inc, nullptr, H.poff, H.pins,
+                                                        nullptr);
     count_launch();
     k_coarse_src<<<grid1d(L.E), 256, 0, s>>>(L.E, L.src, L.sdst, L.gamma, H.noff, H.inn, H.src,
                                              H.sdst);

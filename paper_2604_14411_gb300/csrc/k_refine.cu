@@ -398,6 +398,99 @@ __global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_p
     }
 }
 
+// Edge-centric in-sequence gains (hyperedges of at most kSeqEdgeMax pins): a
+// warp per hyperedge gathers its moving pins (move index, ps, pd, whether the
+// pin is a destination); for every mover it adds up how the movers ordered
+// before it changed pins(ps, e), pins(pd, e) and their destination-only
+// variants, and writes the move's Eq. (1) change on e and its inbound-set
+// changes into the slot of (move, e): slots of move k are I(n_k) in order.
+constexpr int kSeqEdgeMax = 256;
+constexpr int kSeqWarps = 8;
+
+__global__ void k_move_deg1(int32_t M, const int32_t *mv_n, const int32_t *ioff, int32_t *deg) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = mv_n[k];
+        deg[k] = ioff[n + 1] - ioff[n];
+    }
+}
+
+__global__ void __launch_bounds__(kSeqWarps * 32)
+k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *idx_of,
+           const int32_t *mv_n, const int32_t *mv_ps, const int32_t *mv_pd, const int32_t *src,
+           const uint8_t *sdst, const int32_t *ioff, const int32_t *inc, const int32_t *slot0,
+           const int32_t *nrun, const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
+           const int32_t *ew, int32_t *c_gain, uint8_t *c_in) {
+    __shared__ int32_t sk[kSeqWarps][kSeqEdgeMax], sps[kSeqWarps][kSeqEdgeMax];
+    __shared__ int32_t spd[kSeqWarps][kSeqEdgeMax], sn[kSeqWarps][kSeqEdgeMax];
+    __shared__ uint8_t sdt[kSeqWarps][kSeqEdgeMax];
+    const int w = warp_id();
+    const unsigned lt = (1u << lane_id()) - 1u;
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = gw; e < E; e += nw) {
+        int32_t p0 = poff[e], p1 = poff[e + 1];
+        int32_t se = src[e];
+        bool sd = sdst[e] != 0;
+        int32_t cnt = 0;
+        for (int32_t base = p0; base < p1; base += 32) {
+            int32_t j = base + lane_id();
+            int32_t m = j < p1 ? pins[j] : -1;
+            int32_t k = m >= 0 ? idx_of[m] : -1;
+            unsigned ball = __ballot_sync(0xffffffffu, k >= 0);
+            if (k >= 0) {
+                int32_t q = cnt + __popc(ball & lt);
+                sk[w][q] = k; sps[w][q] = mv_ps[k]; spd[w][q] = mv_pd[k]; sn[w][q] = m;
+                sdt[w][q] = (m != se || sd) ? 1 : 0;
+            }
+            cnt += __popc(ball);
+        }
+        __syncwarp();
+        int32_t r0 = poff[e], r1 = r0 + nrun[e];
+        int32_t we = ew[e];
+        for (int32_t i = lane_id(); i < cnt; i += 32) {
+            int32_t ki = sk[w][i], psi = sps[w][i], pdi = spd[w][i];
+            int32_t cs, csi, cd, cdi;
+            run_lookup(rpart, rcnt, rcin, r0, r1, psi, cs, csi);
+            run_lookup(rpart, rcnt, rcin, r0, r1, pdi, cd, cdi);
+            for (int32_t t = 0; t < cnt; ++t) {
+                if (sk[w][t] >= ki) continue;
+                int32_t ps = sps[w][t], pd = spd[w][t];
+                int32_t ds = (pd == psi) - (ps == psi), dd = (pd == pdi) - (ps == pdi);
+                cs += ds; cd += dd;
+                if (sdt[w][t]) { csi += ds; cdi += dd; }
+            }
+            int32_t n = sn[w][i];
+            int32_t pos = lower_bound_i32(inc, ioff[n], ioff[n + 1], (int32_t)e) - ioff[n];
+            int32_t s = slot0[ki] + pos;
+            bool dst = sdt[w][i] != 0;
+            c_gain[s] = we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
+            c_in[s] = (uint8_t)(((dst && csi == 1) ? 1 : 0) | ((dst && cdi == 0) ? 2 : 0));
+        }
+        __syncwarp();
+    }
+}
+
+// per move: gain = sum of its slots; lose / gain_in = counts of the slot bits
+__global__ void k_move_reduce1(int32_t M, const int32_t *slot0, const int32_t *c_gain,
+                               const uint8_t *c_in, int32_t *gseq, int32_t *lose_in,
+                               int32_t *gain_in) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = gw; k < M; k += nw) {
+        int32_t g = 0, lo = 0, gi = 0;
+        for (int32_t j = slot0[k] + lane_id(); j < slot0[k + 1]; j += 32) {
+            g += c_gain[j];
+            lo += c_in[j] & 1;
+            gi += c_in[j] >> 1;
+        }
+        g = warp_sum(g);
+        lo = warp_sum(lo);
+        gi = warp_sum(gi);
+        if (lane_id() == 0) { gseq[k] = g; lose_in[k] = lo; gain_in[k] = gi; }
+    }
+}
+
 __global__ void k_event_ekp(int64_t n, const int32_t *ev_e, const uint32_t *ev_p, int32_t K,
                             uint32_t *key) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -723,7 +816,31 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     fill_i32(idx_of, -1, V, s);
     k_move_info<<<grid1d(M), 256, 0, s>>>(M, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
     count_launch();
-    // in-sequence gains from per-(edge, part) events
+    // in-sequence gains: edge-centric when every hyperedge is small, otherwise
+    // from per-(edge, part) events
+    if (L.max_edge <= kSeqEdgeMax) {
+        int32_t *deg, *slot0, *c_gain;
+        uint8_t *c_in;
+        e = dalloc(tmp, &deg, M);
+        if (!e) e = dalloc(tmp, &slot0, (size_t)M + 1);
+        if (e) return e;
+        k_move_deg1<<<grid1d(M), 256, 0, s>>>(M, mv_n, L.ioff, deg);
+        count_launch();
+        e = counts_to_offsets(tmp, deg, slot0, M, s);
+        if (e) return e;
+        // slots total <= P: size the buffers without a host round trip
+        e = dalloc(tmp, &c_gain, L.P);
+        if (!e) e = dalloc(tmp, &c_in, L.P);
+        if (e) return e;
+        int blocks = div_up((int64_t)L.E * 32, kSeqWarps * 32);
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+        k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_n, mv_ps, mv_pd,
+                                                     L.src, L.sdst, L.ioff, L.inc, slot0, R.nrun,
+                                                     R.rpart, R.rcnt, R.rcin, ew, c_gain, c_in);
+        count_launch();
+        k_move_reduce1<<<grid_warps(M), 256, 0, s>>>(M, slot0, c_gain, c_in, gseq, lose, gin);
+        count_launch();
+    } else
     {
         int32_t *deg, *evoff, *dNev;
         e = dalloc(tmp, &deg, M);

@@ -94,6 +94,12 @@ def test_variable_size_edges(seed):
     compare(synth.random_snn(900, 8, seed, size_max=40), 24, 150)
 
 
+def test_large_hyperedges_use_the_event_path():
+    """Hyperedges above 256 pins route in-sequence gains through the sorted
+    (edge, part) events instead of the per-hyperedge kernel."""
+    compare(synth.random_snn(1500, 8, 12, size_max=300), 40, 2000)
+
+
 def test_conv_style():
     compare(synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400)
 
