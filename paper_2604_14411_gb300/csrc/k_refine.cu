@@ -343,8 +343,9 @@ __global__ void k_move_keys(int32_t V, const int32_t *gain, const int32_t *rank,
     }
 }
 
-__global__ void k_move_info(int32_t M, const int32_t *mv_n, const int32_t *rho, const int32_t *pd,
-                            int32_t *mv_ps, int32_t *mv_pd, int32_t *idx_of) {
+__global__ void k_move_info(int32_t Mcap, const int32_t *dM, const int32_t *mv_n, const int32_t *rho,
+                            const int32_t *pd, int32_t *mv_ps, int32_t *mv_pd, int32_t *idx_of) {
+    const int32_t M = min(*dM, Mcap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
          k += (int64_t)gridDim.x * blockDim.x) {
         int32_t n = mv_n[k];
@@ -407,11 +408,13 @@ __global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_p
 constexpr int kSeqEdgeMax = 256;
 constexpr int kSeqWarps = 8;
 
-__global__ void k_move_deg1(int32_t M, const int32_t *mv_n, const int32_t *ioff, int32_t *deg) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+__global__ void k_move_deg1(int32_t Mcap, const int32_t *dM, const int32_t *mv_n, const int32_t *ioff,
+                            int32_t *deg) {
+    const int32_t M = *dM;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Mcap;
          k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t n = mv_n[k];
-        deg[k] = ioff[n + 1] - ioff[n];
+        int32_t n = k < M ? mv_n[k] : -1;
+        deg[k] = n >= 0 ? ioff[n + 1] - ioff[n] : 0;
     }
 }
 
@@ -472,12 +475,12 @@ k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *i
 }
 
 // per move: gain = sum of its slots; lose / gain_in = counts of the slot bits
-__global__ void k_move_reduce1(int32_t M, const int32_t *slot0, const int32_t *c_gain,
+__global__ void k_move_reduce1(int32_t Mcap, const int32_t *slot0, const int32_t *c_gain,
                                const uint8_t *c_in, int32_t *gseq, int32_t *lose_in,
                                int32_t *gain_in) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = gw; k < M; k += nw) {
+    for (int64_t k = gw; k < Mcap; k += nw) {     // moves past M have no slots: zeros
         int32_t g = 0, lo = 0, gi = 0;
         for (int32_t j = slot0[k] + lane_id(); j < slot0[k + 1]; j += 32) {
             g += c_gain[j];
@@ -587,24 +590,28 @@ __global__ void k_move_reduce(int32_t M, const int32_t *evoff, const int32_t *c_
 }
 
 // events: 2 per move, (ps, k, -w, -lose) then (pd, k, +w, +gain_in)
-__global__ void k_events(int32_t M, const int32_t *mv_n, const int32_t *mv_ps, const int32_t *mv_pd,
-                         const int32_t *w, uint32_t *ekey, int32_t *eid) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+__global__ void k_events(int32_t Mcap, const int32_t *dM, const int32_t *mv_n, const int32_t *mv_ps,
+                         const int32_t *mv_pd, const int32_t *w, uint32_t pad, uint32_t *ekey,
+                         int32_t *eid) {
+    const int32_t M = *dM;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Mcap;
          k += (int64_t)gridDim.x * blockDim.x) {
-        ekey[2 * k] = (uint32_t)mv_ps[k];
-        ekey[2 * k + 1] = (uint32_t)mv_pd[k];
+        ekey[2 * k] = k < M ? (uint32_t)mv_ps[k] : pad;        // padding sorts last
+        ekey[2 * k + 1] = k < M ? (uint32_t)mv_pd[k] : pad;
         eid[2 * k] = (int32_t)(2 * k);
         eid[2 * k + 1] = (int32_t)(2 * k + 1);
     }
 }
 
-__global__ void k_event_deltas(int64_t nev, const int32_t *eid_sorted, const int32_t *mv_n,
-                               const int32_t *w, const int32_t *lose_in, const int32_t *gain_in,
-                               int64_t *dsz, int64_t *dinb) {
+__global__ void k_event_deltas(int64_t nev, const int32_t *dM, const int32_t *eid_sorted,
+                               const int32_t *mv_n, const int32_t *w, const int32_t *lose_in,
+                               const int32_t *gain_in, int64_t *dsz, int64_t *dinb) {
+    const int32_t M = *dM;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t id = eid_sorted[i];
         int32_t k = id >> 1;
+        if (k >= M) { dsz[i] = 0; dinb[i] = 0; continue; }
         bool leave = (id & 1) == 0;
         int32_t wn = w[mv_n[k]];
         dsz[i] = leave ? -wn : wn;
@@ -614,10 +621,12 @@ __global__ void k_event_deltas(int64_t nev, const int32_t *eid_sorted, const int
 
 __global__ void k_transitions(int64_t nev, const uint32_t *ekey_sorted, const int32_t *eid_sorted,
                               const int64_t *csz, const int64_t *cinb, const int32_t *size0,
-                              const int32_t *inb0, int64_t omega, int64_t delta, int32_t *vdelta) {
+                              const int32_t *inb0, int64_t omega, int64_t delta, uint32_t pad,
+                              int32_t *vdelta) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nev;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t p = ekey_sorted[i];
+        if (p == pad) continue;                        // padding events
         // first event of this part
         int64_t lo = 0, hi = i;
         while (lo < hi) {
@@ -655,8 +664,10 @@ __global__ void k_gseq_i64(int32_t M, const int32_t *gseq, const int32_t *vdelta
 
 // single CTA: k* = argmax over valid prefixes of (G, length); apply iff G > 0.
 // stats[0..2] = (M, k*, gain); *applied accumulates k* over passes.
-__global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32_t *kstar,
-                         long long *stats, unsigned long long *applied, int32_t *applied_flag) {
+__global__ void k_select(int32_t Mcap, const int32_t *dM, const int64_t *G, const int64_t *viol,
+                         int32_t *kstar, long long *stats, unsigned long long *applied,
+                         int32_t *applied_flag) {
+    const int32_t M = min(*dM, Mcap);
     __shared__ long long bg[1024];
     __shared__ int32_t bk[1024];
     long long g = 0;
@@ -690,8 +701,9 @@ __global__ void k_select(int32_t M, const int64_t *G, const int64_t *viol, int32
     }
 }
 
-__global__ void k_apply(int32_t M, const int32_t *kstar, const int32_t *mv_n, const int32_t *mv_pd,
+__global__ void k_apply(int32_t Mcap, const int32_t *kstar, const int32_t *mv_n, const int32_t *mv_pd,
                         int32_t *rho) {
+    const int32_t M = Mcap;
     int32_t ks = *kstar;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ks && k < M;
          k += (int64_t)gridDim.x * blockDim.x)
@@ -777,7 +789,9 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         cudaEventCreate(&pt->ev.back().second);
         cudaEventRecord(pt->ev.back().second, s);
     }
-    // compact proposals in node order, read M
+    // compact proposals in node order.  Levels whose hyperedges are small keep
+    // the move count M on the device (arrays sized by V, padding sorted last);
+    // the event path needs M on the host to size its events.
     int32_t *flag, *rank, *dM;
     e = dalloc(tmp, &flag, V);
     if (!e) e = dalloc(tmp, &rank, V);
@@ -787,14 +801,17 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     count_launch();
     e = exclusive_scan_i32(tmp, flag, rank, V, dM, s);
     if (e) return e;
-    int32_t M = 0;
-    e = cudaMemcpyAsync(&M, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaStreamSynchronize(s);
-    if (e) return e;
-    if (M == 0) {
-        e = cudaMemsetAsync(d_stats, 0, 3 * sizeof(long long), s);
-        if (!e) e = cudaMemsetAsync(ru.applied_flag, 0, sizeof(int32_t), s);
-        return e;
+    const bool edge_path = L.max_edge <= kSeqEdgeMax;
+    int32_t M = V;                       // capacity: exact M on the event path
+    if (!edge_path) {
+        e = cudaMemcpyAsync(&M, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return e;
+        if (M == 0) {
+            e = cudaMemsetAsync(d_stats, 0, 3 * sizeof(long long), s);
+            if (!e) e = cudaMemsetAsync(ru.applied_flag, 0, sizeof(int32_t), s);
+            return e;
+        }
     }
     uint32_t *mkey, *mkey2;
     int32_t *mnode, *mv_n, *mv_ps, *mv_pd, *idx_of, *gseq, *lose, *gin;
@@ -809,12 +826,17 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     if (!e) e = dalloc(tmp, &lose, M);
     if (!e) e = dalloc(tmp, &gin, M);
     if (e) return e;
+    const int mbits = bits_for(wsum);
+    if (edge_path) {            // unused slots: maximal key, sorted after every move
+        fill_i32(reinterpret_cast<int32_t *>(mkey), (int32_t)((1u << mbits) - 1u), M, s);
+        fill_i32(mnode, -1, M, s);
+    }
     k_move_keys<<<grid1d(V), 256, 0, s>>>(V, pg, rank, mkey, mnode, wsum);
     count_launch();
-    e = radix_sort_pairs(tmp, mkey, mnode, mkey2, mv_n, M, bits_for(wsum), s);
+    e = radix_sort_pairs(tmp, mkey, mnode, mkey2, mv_n, M, mbits, s);
     if (e) return e;
     fill_i32(idx_of, -1, V, s);
-    k_move_info<<<grid1d(M), 256, 0, s>>>(M, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
+    k_move_info<<<grid1d(M), 256, 0, s>>>(M, dM, mv_n, rho, ppd, mv_ps, mv_pd, idx_of);
     count_launch();
     // in-sequence gains: edge-centric when every hyperedge is small, otherwise
     // from per-(edge, part) events
@@ -824,7 +846,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         e = dalloc(tmp, &deg, M);
         if (!e) e = dalloc(tmp, &slot0, (size_t)M + 1);
         if (e) return e;
-        k_move_deg1<<<grid1d(M), 256, 0, s>>>(M, mv_n, L.ioff, deg);
+        k_move_deg1<<<grid1d(M), 256, 0, s>>>(M, dM, mv_n, L.ioff, deg);
         count_launch();
         e = counts_to_offsets(tmp, deg, slot0, M, s);
         if (e) return e;
@@ -834,6 +856,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         if (e) return e;
         int blocks = div_up((int64_t)L.E * 32, kSeqWarps * 32);
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+        if (blocks < 1) blocks = 1;
         k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_n, mv_ps, mv_pd,
                                                      L.src, L.sdst, L.ioff, L.inc, slot0, R.nrun,
                                                      R.rpart, R.rcnt, R.rcin, ew, c_gain, c_in);
@@ -939,18 +962,20 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     if (!e) e = dalloc(tmp, &G, M);
     if (!e) e = dalloc(tmp, &viol, M);
     if (e) return e;
-    k_events<<<grid1d(M), 256, 0, s>>>(M, mv_n, mv_ps, mv_pd, L.w, ekey, eid);
+    const int pbits = bits_for(K);
+    const uint32_t pad = (1u << pbits) - 1u;          // > every part id
+    k_events<<<grid1d(M), 256, 0, s>>>(M, dM, mv_n, mv_ps, mv_pd, L.w, pad, ekey, eid);
     count_launch();
-    e = radix_sort_pairs(tmp, ekey, eid, ekey2, eid2, nev, bits_for(K > 0 ? K - 1 : 0), s);
+    e = radix_sort_pairs(tmp, ekey, eid, ekey2, eid2, nev, pbits, s);
     if (e) return e;
-    k_event_deltas<<<grid1d(nev), 256, 0, s>>>(nev, eid2, mv_n, L.w, lose, gin, dsz, dinb);
+    k_event_deltas<<<grid1d(nev), 256, 0, s>>>(nev, dM, eid2, mv_n, L.w, lose, gin, dsz, dinb);
     count_launch();
     e = inclusive_scan_i64(tmp, dsz, csz, nev, s);
     if (!e) e = inclusive_scan_i64(tmp, dinb, cinb, nev, s);
     if (e) return e;
     cudaMemsetAsync(vdelta, 0, sizeof(int32_t) * (size_t)M, s);
     k_transitions<<<grid1d(nev), 256, 0, s>>>(nev, ekey2, eid2, csz, cinb, size, inb, omega, delta,
-                                              vdelta);
+                                              pad, vdelta);
     count_launch();
     k_gseq_i64<<<grid1d(M), 256, 0, s>>>(M, gseq, vdelta, g64, v64);
     count_launch();
@@ -960,7 +985,7 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     int32_t *dk;
     e = dalloc(tmp, &dk, 1);
     if (e) return e;
-    k_select<<<1, 1024, 0, s>>>(M, G, viol, dk, d_stats, d_applied, ru.applied_flag);
+    k_select<<<1, 1024, 0, s>>>(M, dM, G, viol, dk, d_stats, d_applied, ru.applied_flag);
     count_launch();
     k_apply<<<grid1d(M), 256, 0, s>>>(M, dk, mv_n, mv_pd, rho);
     count_launch();
