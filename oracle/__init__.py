@@ -30,6 +30,8 @@ OK, INVALID, INFEASIBLE, OOM, INTERNAL = 0, 1, 2, 3, 4
 A_PAIR, A_SCORE, A_MATCH, A_GAMMA, A_RHO_IN, A_RHO_OUT, A_W = 0, 1, 2, 3, 4, 5, 6
 A_PINS_OFF, A_PINS, A_INC_OFF, A_INC, A_IN_OFF, A_IN = 7, 8, 9, 10, 11, 12
 A_MOVE_N, A_MOVE_PS, A_MOVE_PD, A_MOVE_GAIN, A_GAIN_SEQ, A_VIOL = 13, 14, 15, 16, 17, 18
+A_KEY = 19
+N_PARAMS = 641          # W1 (64 x 8), b1 (64), W2 (64), b2
 
 
 class OracleError(RuntimeError):
@@ -42,7 +44,8 @@ def build() -> str:
     """Compile the oracle with gcc (plain C11, -O2)."""
     if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", _SRC,
+                               "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -77,6 +80,18 @@ def _load():
             lib.oracle_gamma.restype = i32
             lib.orun_refine0.argtypes = [vp, vp, i32, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orun_contract0.argtypes = [vp, vp]
+            u16, u64, f64 = ctypes.c_uint16, ctypes.c_uint64, ctypes.c_double
+            lib.oracle_match64.argtypes = [i32, vp, vp, i32, vp]
+            lib.orun_partition_learned.argtypes = [vp, i64, i64, i32, vp, vp, vp, u16, i32]
+            lib.oracle_lg1p.argtypes = [i64]
+            lib.oracle_lg1p.restype = ctypes.c_float
+            lib.oracle_mlp.argtypes = [vp, vp, vp, u16, i32, vp, vp, vp]
+            lib.orun_features0.argtypes = [vp, i32, i32, vp]
+            lib.orun_learn_samples.argtypes = [vp, vp, u64, i32, vp, vp, vp]
+            lib.oracle_splitmix64_at.argtypes = [u64, u64]
+            lib.oracle_splitmix64_at.restype = u64
+            lib.oracle_train_step.argtypes = [vp, vp, vp, i64, f64, f64, f64, f64, i32, vp, vp,
+                                              vp, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -144,6 +159,42 @@ class Run:
         inb = np.empty(max(np_, 1), dtype=np.int32)
         lib.orun_part_stats(self._h, _p(w), _p(inb))
         return Result(ids, int(lib.orun_cost(self._h)), int(np_), w[:np_], inb[:np_])
+
+    def partition_learned(self, omega: int, delta: int, model, refine_passes: int = 1) -> Result:
+        """The method with the learned candidate order; `model` has bfloat16
+        bit arrays w1 [64, 8], b1 [64], w2 [64], the scalar b2 and key_bits."""
+        lib = _load()
+        w1, b1, w2 = _model_arrays(model)
+        rc = lib.orun_partition_learned(self._h, int(omega), int(delta), int(refine_passes),
+                                        _p(w1), _p(b1), _p(w2), int(model.b2), int(model.key_bits))
+        if rc:
+            raise OracleError(rc, "partition_learned")
+        np_ = lib.orun_num_parts(self._h)
+        ids = np.empty(self.num_nodes, dtype=np.int32)
+        lib.orun_part_ids(self._h, _p(ids))
+        w = np.empty(max(np_, 1), dtype=np.int64)
+        inb = np.empty(max(np_, 1), dtype=np.int32)
+        lib.orun_part_stats(self._h, _p(w), _p(inb))
+        return Result(ids, int(lib.orun_cost(self._h)), int(np_), w[:np_], inb[:np_])
+
+    def features0(self, n, m):
+        x = np.empty(8, dtype=np.float32)
+        rc = _load().orun_features0(self._h, int(n), int(m), _p(x))
+        if rc:
+            raise OracleError(rc, "features0")
+        return x
+
+    def learn_samples(self, part_ids, seed, per_node):
+        """Training pairs labelled by part_ids: (x [N*per_node, 8], y, partner)."""
+        S = self.num_nodes * int(per_node)
+        x = np.empty((S, 8), dtype=np.float32)
+        y = np.empty(S, dtype=np.float32)
+        partner = np.empty(S, dtype=np.int32)
+        rc = _load().orun_learn_samples(self._h, _p(_i32(part_ids)), ctypes.c_uint64(int(seed)),
+                                        int(per_node), _p(x), _p(y), _p(partner))
+        if rc:
+            raise OracleError(rc, "learn_samples")
+        return x, y, partner
 
     # ---- trace ----
     @property
@@ -254,3 +305,65 @@ def gamma(match_arr):
 def partition(g, omega, delta, refine_passes=1) -> Result:
     with Run.from_graph(g) as r:
         return r.partition(omega, delta, refine_passes)
+
+
+def _model_arrays(model):
+    w1 = np.ascontiguousarray(model.w1, dtype=np.uint16).reshape(64, 8)
+    b1 = np.ascontiguousarray(model.b1, dtype=np.uint16).reshape(64)
+    w2 = np.ascontiguousarray(model.w2, dtype=np.uint16).reshape(64)
+    return w1, b1, w2
+
+
+def match64(pair, score64, method: int = 0):
+    pair = _i32(pair)
+    s = np.ascontiguousarray(score64, dtype=np.int64)
+    out = np.empty(len(pair), dtype=np.int32)
+    rc = _load().oracle_match64(len(pair), _p(pair), _p(s), int(method), _p(out))
+    if rc:
+        raise OracleError(rc, "match64")
+    return out
+
+
+def lg1p(x: int) -> float:
+    return float(_load().oracle_lg1p(int(x)))
+
+
+def mlp(model, x):
+    """(score, key) of one feature vector under `model`."""
+    w1, b1, w2 = _model_arrays(model)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    s = ctypes.c_float()
+    k = ctypes.c_int32()
+    rc = _load().oracle_mlp(_p(w1), _p(b1), _p(w2), int(model.b2), int(model.key_bits), _p(xx),
+                            ctypes.byref(s), ctypes.byref(k))
+    if rc:
+        raise OracleError(rc, "mlp")
+    return s.value, k.value
+
+
+def train_step(params, x, y, lr, beta1, beta2, eps, t, m, v):
+    """One Adam step in double precision; returns dict(grad, loss, params, m, v)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    yy = np.ascontiguousarray(y, dtype=np.float32)
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    out = {k: np.empty(N_PARAMS) for k in ("grad", "params", "m", "v")}
+    loss = ctypes.c_double()
+    rc = _load().oracle_train_step(_p(p), _p(xx), _p(yy), len(yy), float(lr), float(beta1),
+                                   float(beta2), float(eps), int(t), _p(mm), _p(vv),
+                                   _p(out["grad"]), ctypes.byref(loss), _p(out["params"]),
+                                   _p(out["m"]), _p(out["v"]))
+    if rc:
+        raise OracleError(rc, "train_step")
+    out["loss"] = loss.value
+    return out
+
+
+def partition_learned(g, omega, delta, model, refine_passes=1) -> Result:
+    with Run.from_graph(g) as r:
+        return r.partition_learned(omega, delta, model, refine_passes)
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    return int(_load().oracle_splitmix64_at(ctypes.c_uint64(seed), ctypes.c_uint64(i)))

@@ -26,6 +26,7 @@
  * Integers throughout: node/edge ids int32, weights int32 on input, sums
  * int64.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -256,10 +257,183 @@ static int score_level(const olevel *g, const int32_t *ew, int64_t omega,
 }
 
 /* ------------------------------------------------------------------ */
+/* Learned merge proposal (an extension; the paper has none).          */
+/* ------------------------------------------------------------------ */
+/*
+ * A two-layer network reorders the candidates of Eq. (2):
+ *   x      = 8 features of the pair (n, m), symmetric in n and m (below)
+ *   h_j    = max(0, b1_j + sum_i W1_ji x_i)            j = 0..63
+ *   s      = b2 + sum_j W2_j h_j
+ *   key    = floor(s * 2^key_bits), clamped to [-2^30, 2^30]
+ * Weights are bfloat16 bit patterns, widened exactly to float.  Every sum is
+ * evaluated in float32 as a chain of fused multiply-adds in index order
+ * (h_j over i = 0..7, then s over j = 0..63, each h_j folded in as soon as it
+ * is known); this order is part of the definition, so any implementation
+ * that follows it gets bit-identical keys.
+ * pair(n) = the valid m (same two checks as Sec. III-B.2) with the largest
+ * (key, hist, id); score(n) = hist(n, pair(n)).  With every weight zero all
+ * keys are equal and the order is the plain (hist, id) order.
+ * Because (key, hist) is symmetric in n and m, every cycle of the pairing
+ * graph is a two-cycle by the same argument as for hist alone, and matching
+ * runs on the composite (key, hist) score.
+ *
+ * Features, each through lg1p (log2(1 + x) with a linear mantissa):
+ *   x0 hist(n,m)          x1 |in(n) u in(m)|
+ *   x2 min(|I(n)|,|I(m)|) x3 max(|I(n)|,|I(m)|)
+ *   x4 min(|in(n)|,|in(m)|) x5 max(|in(n)|,|in(m)|)
+ *   x6 min(w(n),w(m))     x7 max(w(n),w(m))
+ */
+#define OMLP_IN 8
+#define OMLP_HID 64
+#define OMLP_PARAMS (OMLP_HID * OMLP_IN + OMLP_HID + OMLP_HID + 1)
+
+typedef struct {
+    float w1[OMLP_HID][OMLP_IN], b1[OMLP_HID], w2[OMLP_HID], b2;
+    int32_t key_bits;
+} omodel;
+
+static float bf16_to_f32(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
+/* 2^k as a float, exact for -126 <= k <= 127. */
+static float pow2f_exact(int k) {
+    uint32_t u = (uint32_t)(127 + k) << 23;
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
+/* log2(1 + x) for integer x >= 0, with the mantissa taken linearly: if
+ * 2^k <= 1 + x < 2^(k+1) the value is k + (1 + x - 2^k) / 2^k.  Exact at
+ * every power of two and at most 0.0861 below log2(1 + x) elsewhere.  The
+ * integer remainder is rounded to float once (round to nearest even); the
+ * division by 2^k is exact. */
+static float lg1p(int64_t x) {
+    uint64_t y = (uint64_t)x + 1u;
+    int k = 0;
+    while (k < 63 && (y >> (k + 1)) != 0) ++k;
+    float frac = (float)(y - ((uint64_t)1 << k)) * pow2f_exact(-k);
+    return (float)k + frac;
+}
+
+static float mlp_score(const omodel *M, const float *x) {
+    float s = M->b2;
+    for (int j = 0; j < OMLP_HID; ++j) {
+        float h = M->b1[j];
+        for (int i = 0; i < OMLP_IN; ++i) h = fmaf(M->w1[j][i], x[i], h);
+        h = h > 0.0f ? h : 0.0f;
+        s = fmaf(M->w2[j], h, s);
+    }
+    return s;
+}
+
+static int32_t score_key(float s, int32_t key_bits) {
+    float q = floorf(s * pow2f_exact(key_bits));
+    if (!(q > -1073741824.0f)) return -1073741824;     /* also NaN */
+    if (q > 1073741824.0f) return 1073741824;
+    return (int32_t)q;
+}
+
+static int model_from_bits(const uint16_t *w1, const uint16_t *b1, const uint16_t *w2, uint16_t b2,
+                           int32_t key_bits, omodel *M) {
+    if (key_bits < 0 || key_bits > 20) return ORC_INVALID;
+    for (int j = 0; j < OMLP_HID; ++j) {
+        for (int i = 0; i < OMLP_IN; ++i) M->w1[j][i] = bf16_to_f32(w1[j * OMLP_IN + i]);
+        M->b1[j] = bf16_to_f32(b1[j]);
+        M->w2[j] = bf16_to_f32(w2[j]);
+    }
+    M->b2 = bf16_to_f32(b2);
+    M->key_bits = key_bits;
+    return ORC_OK;
+}
+
+/* |in(n) u in(m)| with in(n) marked in `stamp`. */
+static int64_t union_size(const olevel *g, int32_t n, int32_t m, const int32_t *stamp) {
+    int64_t u = g->noff[n + 1] - g->noff[n];
+    for (int64_t j = g->noff[m]; j < g->noff[m + 1]; ++j) u += stamp[g->in[j]] != n;
+    return u;
+}
+
+static void pair_features(const olevel *g, int32_t n, int32_t m, int64_t hist, int64_t uni, float *x) {
+    int64_t dn = g->ioff[n + 1] - g->ioff[n], dm = g->ioff[m + 1] - g->ioff[m];
+    int64_t in_n = g->noff[n + 1] - g->noff[n], in_m = g->noff[m + 1] - g->noff[m];
+    int64_t wn = g->w[n], wm = g->w[m];
+    x[0] = lg1p(hist);
+    x[1] = lg1p(uni);
+    x[2] = lg1p(dn < dm ? dn : dm);
+    x[3] = lg1p(dn < dm ? dm : dn);
+    x[4] = lg1p(in_n < in_m ? in_n : in_m);
+    x[5] = lg1p(in_n < in_m ? in_m : in_n);
+    x[6] = lg1p(wn < wm ? wn : wm);
+    x[7] = lg1p(wn < wm ? wm : wn);
+}
+
+static void score_node_learned(const olevel *g, const int32_t *ew, int64_t omega, int64_t delta,
+                               const omodel *M, int32_t n, int32_t *pair, int32_t *score,
+                               int32_t *key, int64_t *hist_scratch, int32_t *touched,
+                               int32_t *stamp) {
+    int32_t nt = 0;
+    for (int64_t i = g->ioff[n]; i < g->ioff[n + 1]; ++i) {
+        int32_t e = g->inc[i];
+        int64_t we = ew ? ew[e] : 1;
+        for (int64_t j = g->poff[e]; j < g->poff[e + 1]; ++j) {
+            int32_t m = g->pins[j];
+            if (m == n) continue;
+            if (hist_scratch[m] == 0) touched[nt++] = m;
+            hist_scratch[m] += we;
+        }
+    }
+    for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = n;
+    int32_t best = -1, bk = 0;
+    int64_t bh = 0;
+    for (int32_t t = 0; t < nt; ++t) {
+        int32_t m = touched[t];
+        if (g->w[n] + g->w[m] > omega) continue;
+        int64_t uni = union_size(g, n, m, stamp);
+        if (uni > delta) continue;
+        float x[OMLP_IN];
+        pair_features(g, n, m, hist_scratch[m], uni, x);
+        int32_t k = score_key(mlp_score(M, x), M->key_bits);
+        int64_t h = hist_scratch[m];
+        if (best < 0 || k > bk || (k == bk && (h > bh || (h == bh && m > best)))) {
+            best = m; bk = k; bh = h;
+        }
+    }
+    *pair = best;
+    *score = best >= 0 ? (int32_t)bh : 0;
+    *key = best >= 0 ? bk : 0;
+    for (int32_t t = 0; t < nt; ++t) hist_scratch[touched[t]] = 0;
+}
+
+static int score_level_learned(const olevel *g, const int32_t *ew, int64_t omega, int64_t delta,
+                               const omodel *M, int32_t *pair, int32_t *score, int32_t *key,
+                               int64_t *hist_scratch, int32_t *touched) {
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!stamp) return ORC_OOM;
+    for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
+    for (int32_t n = 0; n < g->V; ++n)
+        score_node_learned(g, ew, omega, delta, M, n, pair + n, score + n, key + n, hist_scratch,
+                           touched, stamp);
+    free(stamp);
+    return ORC_OK;
+}
+
+/* Composite matching score of the learned order: (key, hist) as one int64. */
+static int64_t learned_composite(int32_t key, int32_t hist) {
+    return ((int64_t)key + 1073741824) * ((int64_t)1 << 32) + (int64_t)hist;
+}
+
+/* ------------------------------------------------------------------ */
 /* Matching over the pairing pseudo-forest (Sec. III-A, III-B.3).      */
 /* ------------------------------------------------------------------ */
-static int beats(const int32_t *score, int32_t a, int32_t b) {
-    /* (score(a), a) > (score(b), b): ties on score broken by the larger id. */
+static int beats(const int64_t *score, int32_t a, int32_t b) {
+    /* (score(a), a) > (score(b), b): ties on score broken by the larger id.
+     * Scores are int64 so that the learned order's composite (key, hist)
+     * compares the same way. */
     return score[a] > score[b] || (score[a] == score[b] && a > b);
 }
 
@@ -274,7 +448,7 @@ static int beats(const int32_t *score, int32_t a, int32_t b) {
  * Returns ORC_INTERNAL if the pairing graph has a cycle longer than two,
  * which the paper shows cannot happen.
  */
-static int match_walks(int32_t V, const int32_t *pair, const int32_t *score, int32_t *match) {
+static int match_walks(int32_t V, const int32_t *pair, const int64_t *score, int32_t *match) {
     int32_t *depth = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
     int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
@@ -328,7 +502,7 @@ static int match_walks(int32_t V, const int32_t *pair, const int32_t *score, int
  * lock(n) = [best(pair(n)) = n] and not lock(pair(n)).
  * match(n) = pair(n) if lock(n); else best(n) if n has a child; else n.
  */
-static int match_locks(int32_t V, const int32_t *pair, const int32_t *score, int32_t *match) {
+static int match_locks(int32_t V, const int32_t *pair, const int64_t *score, int32_t *match) {
     int32_t *best = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
     signed char *lock = (signed char *)malloc((size_t)V);
     int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
@@ -629,12 +803,15 @@ typedef struct {
     int32_t cap;
     olevel *G;                    /* G[0] = input hypergraph */
     int32_t **pair, **score, **match, **gamma, **rho_in, **rho_out;
+    int32_t **key;                /* learned order only: key(n, pair(n)) */
     rtrace *rt;                   /* trace of the last pass at each level */
     int32_t nlev;                 /* levels built (L + 1) */
     int32_t top_is_gamma;         /* coarsest level ended by the node target */
     int32_t K;                    /* part-id range during refinement */
     int32_t *src;                 /* src(e) of the input */
     int32_t *ew;                  /* edge weights or NULL (unit) */
+    int32_t *in_off, *in_pins;    /* the input CSR as given (pin order kept) */
+    const omodel *model;          /* learned order, or NULL for Eq. (2) */
     int32_t *part_ids;            /* [N] final, compacted */
     int64_t *part_weight;         /* [num_parts] */
     int32_t *part_inbound;        /* [num_parts] */
@@ -647,9 +824,9 @@ static void orun_clear(orun *r) {
     for (int l = 0; l < r->cap; ++l) {
         if (l > 0) olevel_free(&r->G[l]);
         free(r->pair[l]); free(r->score[l]); free(r->match[l]); free(r->gamma[l]);
-        free(r->rho_in[l]); free(r->rho_out[l]);
+        free(r->rho_in[l]); free(r->rho_out[l]); free(r->key[l]);
         free(r->rt[l].moves); free(r->rt[l].gain_seq); free(r->rt[l].viol);
-        r->pair[l] = r->score[l] = r->match[l] = r->gamma[l] = NULL;
+        r->pair[l] = r->score[l] = r->match[l] = r->gamma[l] = r->key[l] = NULL;
         r->rho_in[l] = r->rho_out[l] = NULL;
         memset(&r->rt[l], 0, sizeof(rtrace));
     }
@@ -671,13 +848,27 @@ int orun_create(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pin
     r->gamma = (int32_t **)calloc((size_t)r->cap, sizeof(int32_t *));
     r->rho_in = (int32_t **)calloc((size_t)r->cap, sizeof(int32_t *));
     r->rho_out = (int32_t **)calloc((size_t)r->cap, sizeof(int32_t *));
+    r->key = (int32_t **)calloc((size_t)r->cap, sizeof(int32_t *));
     r->rt = (rtrace *)calloc((size_t)r->cap, sizeof(rtrace));
     int rc = ORC_OOM;
-    if (r->G && r->pair && r->score && r->match && r->gamma && r->rho_in && r->rho_out && r->rt)
+    if (r->G && r->pair && r->score && r->match && r->gamma && r->rho_in && r->rho_out && r->key && r->rt)
         rc = build_level0(N, E, offsets, pins, node_w, edge_w, &r->G[0], &r->src);
+    if (!rc) {
+        r->in_off = (int32_t *)malloc(sizeof(int32_t) * ((size_t)E + 1));
+        r->in_pins = (int32_t *)malloc(sizeof(int32_t) * (size_t)(offsets[E] > 0 ? offsets[E] : 1));
+        if (!r->in_off || !r->in_pins) {
+            rc = ORC_OOM;
+            olevel_free(&r->G[0]);
+            free(r->src);
+        } else {
+            memcpy(r->in_off, offsets, sizeof(int32_t) * ((size_t)E + 1));
+            memcpy(r->in_pins, pins, sizeof(int32_t) * (size_t)offsets[E]);
+        }
+    }
     if (rc) {
+        free(r->in_off); free(r->in_pins);
         free(r->G); free(r->pair); free(r->score); free(r->match); free(r->gamma);
-        free(r->rho_in); free(r->rho_out); free(r->rt); free(r);
+        free(r->rho_in); free(r->rho_out); free(r->key); free(r->rt); free(r);
         return rc;
     }
     r->nlev = 1;
@@ -694,9 +885,9 @@ void orun_destroy(orun *r) {
     if (!r) return;
     orun_clear(r);
     olevel_free(&r->G[0]);
-    free(r->src); free(r->ew);
+    free(r->src); free(r->ew); free(r->in_off); free(r->in_pins);
     free(r->G); free(r->pair); free(r->score); free(r->match); free(r->gamma);
-    free(r->rho_in); free(r->rho_out); free(r->rt);
+    free(r->rho_in); free(r->rho_out); free(r->key); free(r->rt);
     free(r);
 }
 
@@ -718,7 +909,7 @@ static int64_t connectivity(const olevel *g, const int32_t *ew, const int32_t *r
     return c;
 }
 
-int orun_partition(orun *r, int64_t omega, int64_t delta, int32_t refine_passes) {
+static int partition_impl(orun *r, int64_t omega, int64_t delta, int32_t refine_passes) {
     if (omega < 1 || delta < 0 || refine_passes < 0) return ORC_INVALID;
     orun_clear(r);
     olevel *G0 = &r->G[0];
@@ -750,10 +941,22 @@ int orun_partition(orun *r, int64_t omega, int64_t delta, int32_t refine_passes)
             if (!r->pair[l] || !r->score[l] || !r->match[l] || !hist || !touched) {
                 free(hist); free(touched); rc = ORC_OOM; goto fail;
             }
-            rc = score_level(g, r->ew, omega, delta, r->pair[l], r->score[l], hist, touched, NULL, 0);
+            int64_t *mscore = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+            if (r->model) r->key[l] = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+            if (!mscore || (r->model && !r->key[l])) {
+                free(hist); free(touched); free(mscore); rc = ORC_OOM; goto fail;
+            }
+            if (r->model)
+                rc = score_level_learned(g, r->ew, omega, delta, r->model, r->pair[l], r->score[l],
+                                         r->key[l], hist, touched);
+            else
+                rc = score_level(g, r->ew, omega, delta, r->pair[l], r->score[l], hist, touched, NULL, 0);
             free(hist); free(touched);
-            if (rc) goto fail;
-            rc = match_walks(V, r->pair[l], r->score[l], r->match[l]);
+            if (rc) { free(mscore); goto fail; }
+            for (int32_t n = 0; n < V; ++n)
+                mscore[n] = r->model ? learned_composite(r->key[l][n], r->score[l][n]) : r->score[l][n];
+            rc = match_walks(V, r->pair[l], mscore, r->match[l]);
+            free(mscore);
             if (rc) goto fail;
             int32_t matched = 0;
             for (int32_t n = 0; n < V; ++n) matched += r->match[l][n] != n;
@@ -861,12 +1064,31 @@ fail:
     return rc;
 }
 
+/* The method as printed (Eq. (2) order). */
+int orun_partition(orun *r, int64_t omega, int64_t delta, int32_t refine_passes) {
+    r->model = NULL;
+    return partition_impl(r, omega, delta, refine_passes);
+}
+
+/* The same with the learned candidate order (model as bfloat16 bits). */
+int orun_partition_learned(orun *r, int64_t omega, int64_t delta, int32_t refine_passes,
+                           const uint16_t *w1, const uint16_t *b1, const uint16_t *w2, uint16_t b2,
+                           int32_t key_bits) {
+    omodel M;
+    int rc = model_from_bits(w1, b1, w2, b2, key_bits, &M);
+    if (rc) return rc;
+    r->model = &M;
+    rc = partition_impl(r, omega, delta, refine_passes);
+    r->model = NULL;
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Accessors (read-only views for the test suite).                     */
 /* ------------------------------------------------------------------ */
 enum {
     ORC_A_PAIR = 0, ORC_A_SCORE = 1, ORC_A_MATCH = 2, ORC_A_GAMMA = 3,
-    ORC_A_RHO_IN = 4, ORC_A_RHO_OUT = 5, ORC_A_W = 6,
+    ORC_A_RHO_IN = 4, ORC_A_RHO_OUT = 5, ORC_A_W = 6, ORC_A_KEY = 19,
     ORC_A_PINS_OFF = 7, ORC_A_PINS = 8, ORC_A_INC_OFF = 9, ORC_A_INC = 10,
     ORC_A_IN_OFF = 11, ORC_A_IN = 12,
     ORC_A_MOVE_N = 13, ORC_A_MOVE_PS = 14, ORC_A_MOVE_PD = 15, ORC_A_MOVE_GAIN = 16,
@@ -896,6 +1118,7 @@ int64_t orun_array_len(const orun *r, int32_t l, int32_t which) {
     case ORC_A_GAMMA: return r->gamma[l] ? g->V : -1;
     case ORC_A_RHO_IN: return r->rho_in[l] ? g->V : -1;
     case ORC_A_RHO_OUT: return r->rho_out[l] ? g->V : -1;
+    case ORC_A_KEY: return r->key[l] ? g->V : -1;
     case ORC_A_W: return g->V;
     case ORC_A_PINS_OFF: return (int64_t)g->E + 1;
     case ORC_A_PINS: return g->poff[g->E];
@@ -923,6 +1146,7 @@ int orun_array(const orun *r, int32_t l, int32_t which, int64_t *out) {
         case ORC_A_GAMMA: v = r->gamma[l][i]; break;
         case ORC_A_RHO_IN: v = r->rho_in[l][i]; break;
         case ORC_A_RHO_OUT: v = r->rho_out[l][i]; break;
+        case ORC_A_KEY: v = r->key[l][i]; break;
         case ORC_A_W: v = g->w[i]; break;
         case ORC_A_PINS_OFF: v = g->poff[i]; break;
         case ORC_A_PINS: v = g->pins[i]; break;
@@ -1001,6 +1225,16 @@ int orun_score0_nodes(const orun *r, int64_t omega, int64_t delta, const int32_t
 /* Matching of an arbitrary pairing graph; method 0 = the two walks,
  * method 1 = the lock recursion. */
 int oracle_match(int32_t V, const int32_t *pair, const int32_t *score, int32_t method, int32_t *match) {
+    int64_t *s64 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V > 0 ? V : 1));
+    if (!s64) return ORC_OOM;
+    for (int32_t n = 0; n < V; ++n) s64[n] = score[n];
+    int rc = method == 0 ? match_walks(V, pair, s64, match) : match_locks(V, pair, s64, match);
+    free(s64);
+    return rc;
+}
+
+/* Same with int64 scores (the learned order's composite keys). */
+int oracle_match64(int32_t V, const int32_t *pair, const int64_t *score, int32_t method, int32_t *match) {
     return method == 0 ? match_walks(V, pair, score, match) : match_locks(V, pair, score, match);
 }
 
@@ -1046,3 +1280,176 @@ int orun_contract0(orun *r, const int32_t *match) {
     r->nlev = 2;
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned order: single steps and training (for the pinning tests).   */
+/* ------------------------------------------------------------------ */
+float oracle_lg1p(int64_t x) { return lg1p(x); }
+
+/* Network score and key of one feature vector. */
+int oracle_mlp(const uint16_t *w1, const uint16_t *b1, const uint16_t *w2, uint16_t b2,
+               int32_t key_bits, const float *x, float *score, int32_t *key) {
+    omodel M;
+    int rc = model_from_bits(w1, b1, w2, b2, key_bits, &M);
+    if (rc) return rc;
+    *score = mlp_score(&M, x);
+    *key = score_key(*score, key_bits);
+    return ORC_OK;
+}
+
+/* Features of the level-0 pair (n, m), m != n: hist as the weight of
+ * I(n) n I(m) (a merge of the two sorted lists), the union by marking. */
+static void features0(const orun *r, int32_t n, int32_t m, int32_t *stamp, float *x) {
+    const olevel *g = &r->G[0];
+    int64_t h = 0, a = g->ioff[n], b = g->ioff[m];
+    while (a < g->ioff[n + 1] && b < g->ioff[m + 1]) {
+        if (g->inc[a] < g->inc[b]) ++a;
+        else if (g->inc[a] > g->inc[b]) ++b;
+        else { h += r->ew ? r->ew[g->inc[a]] : 1; ++a; ++b; }
+    }
+    for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = n;
+    int64_t uni = union_size(g, n, m, stamp);
+    for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = -1;
+    pair_features(g, n, m, h, uni, x);
+}
+
+int orun_features0(const orun *r, int32_t n, int32_t m, float *x) {
+    const olevel *g = &r->G[0];
+    if (n < 0 || m < 0 || n >= g->V || m >= g->V || n == m) return ORC_INVALID;
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!stamp) return ORC_OOM;
+    for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
+    features0(r, n, m, stamp, x);
+    free(stamp);
+    return ORC_OK;
+}
+
+/* The i-th output (i >= 0) of the SplitMix64 generator started at `seed`
+ * (Steele, Lea and Flood, 2014): the state advances by the golden-ratio
+ * increment before each output, which is then mixed by two xor-shift-
+ * multiply rounds and a final xor-shift. */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/*
+ * Training pairs for the learned order, labelled by a partition of the
+ * input (part_ids): slot s = n * per_node + k (k < per_node) draws
+ *   u0 = splitmix64_at(seed, 2 s), u1 = splitmix64_at(seed, 2 s + 1),
+ *   e  = the (u0 mod |I(n)|)-th hyperedge of I(n) (ascending ids),
+ *   m  = the (u1 mod |pins(e)|)-th pin of e in the input's pin order,
+ * so neighbours are drawn in proportion to the hyperedges they share with n.
+ * The slot holds the features of (n, m), label 1 if both are in the same
+ * part, else 0; label -1 (no sample) when m = n or I(n) is empty.
+ */
+int orun_learn_samples(const orun *r, const int32_t *part_ids, uint64_t seed, int32_t per_node,
+                       float *x, float *y, int32_t *partner) {
+    const olevel *g = &r->G[0];
+    if (per_node < 1) return ORC_INVALID;
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!stamp) return ORC_OOM;
+    for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
+    for (int32_t n = 0; n < g->V; ++n) {
+        for (int32_t k = 0; k < per_node; ++k) {
+            int64_t s = (int64_t)n * per_node + k;
+            float *xs = x + s * OMLP_IN;
+            int64_t deg = g->ioff[n + 1] - g->ioff[n];
+            int32_t m = n;
+            if (deg > 0) {
+                uint64_t u0 = splitmix64_at(seed, 2u * (uint64_t)s);
+                uint64_t u1 = splitmix64_at(seed, 2u * (uint64_t)s + 1u);
+                int32_t e = g->inc[g->ioff[n] + (int64_t)(u0 % (uint64_t)deg)];
+                int64_t sz = r->in_off[e + 1] - r->in_off[e];
+                m = r->in_pins[r->in_off[e] + (int64_t)(u1 % (uint64_t)sz)];
+            }
+            if (m == n) {
+                for (int i = 0; i < OMLP_IN; ++i) xs[i] = 0.0f;
+                y[s] = -1.0f;
+                if (partner) partner[s] = -1;
+                continue;
+            }
+            features0(r, n, m, stamp, xs);
+            y[s] = part_ids[n] == part_ids[m] ? 1.0f : 0.0f;
+            if (partner) partner[s] = m;
+        }
+    }
+    free(stamp);
+    return ORC_OK;
+}
+
+/* float -> bfloat16 -> float with round-to-nearest-even on the dropped 16 bits. */
+static double round_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, sizeof(u));
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, sizeof(r));
+    return (double)r;
+}
+
+/*
+ * One training step of the learned order's network, in double precision:
+ * parameters p (float32 master copy; layout W1[j][i] at 8 j + i, then b1,
+ * W2, b2 -- 641 values) are rounded to bfloat16 for the forward pass; the
+ * loss is the mean over samples with label >= 0 of the logistic loss
+ * log(1 + e^s) - y s; its gradient is taken by backpropagation (ReLU
+ * derivative 1 where the pre-activation is > 0) and applied to the master
+ * copy with Adam (Kingma and Ba, 2015) at step t >= 1:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ */
+int oracle_train_step(const float *p, const float *x, const float *y, int64_t count, double lr,
+                      double beta1, double beta2, double eps, int32_t t, const double *m_in,
+                      const double *v_in, double *grad, double *loss, double *p_out,
+                      double *m_out, double *v_out) {
+    if (count < 0 || t < 1) return ORC_INVALID;
+    double W1[OMLP_HID][OMLP_IN], B1[OMLP_HID], W2[OMLP_HID], B2;
+    for (int j = 0; j < OMLP_HID; ++j) {
+        for (int i = 0; i < OMLP_IN; ++i) W1[j][i] = round_bf16(p[j * OMLP_IN + i]);
+        B1[j] = round_bf16(p[512 + j]);
+        W2[j] = round_bf16(p[576 + j]);
+    }
+    B2 = round_bf16(p[640]);
+    for (int q = 0; q < OMLP_PARAMS; ++q) grad[q] = 0.0;
+    double total = 0.0;
+    int64_t valid = 0;
+    for (int64_t s = 0; s < count; ++s) {
+        if (y[s] < 0.0f) continue;
+        const float *xs = x + s * OMLP_IN;
+        double a[OMLP_HID], h[OMLP_HID], out = B2;
+        for (int j = 0; j < OMLP_HID; ++j) {
+            a[j] = B1[j];
+            for (int i = 0; i < OMLP_IN; ++i) a[j] += W1[j][i] * (double)xs[i];
+            h[j] = a[j] > 0.0 ? a[j] : 0.0;
+            out += W2[j] * h[j];
+        }
+        double yy = (double)y[s];
+        total += (out > 0.0 ? out : 0.0) - out * yy + log1p(exp(-fabs(out)));
+        double ds = 1.0 / (1.0 + exp(-out)) - yy;
+        for (int j = 0; j < OMLP_HID; ++j) {
+            grad[576 + j] += ds * h[j];
+            double da = a[j] > 0.0 ? ds * W2[j] : 0.0;
+            for (int i = 0; i < OMLP_IN; ++i) grad[j * OMLP_IN + i] += da * (double)xs[i];
+            grad[512 + j] += da;
+        }
+        grad[640] += ds;
+        valid++;
+    }
+    if (valid > 0) {
+        for (int q = 0; q < OMLP_PARAMS; ++q) grad[q] /= (double)valid;
+        total /= (double)valid;
+    }
+    *loss = total;
+    double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    for (int q = 0; q < OMLP_PARAMS; ++q) {
+        m_out[q] = beta1 * m_in[q] + (1.0 - beta1) * grad[q];
+        v_out[q] = beta2 * v_in[q] + (1.0 - beta2) * grad[q] * grad[q];
+        p_out[q] = (double)p[q] - lr * (m_out[q] / c1) / (sqrt(v_out[q] / c2) + eps);
+    }
+    return ORC_OK;
+}
+
+uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }

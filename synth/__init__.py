@@ -166,3 +166,53 @@ def batch_instances(count: int = 64, seed: int = 0) -> list[Hypergraph]:
             ch = max(1, n // (8 * 256))
             out.append(conv_snn(8, 16, ch, max(1, math.ceil(0.88 * ch)), ch, seed * 1000 + i))
     return out
+
+
+# ---------------- models for the learned candidate order ----------------
+
+@dataclass
+class Model:
+    """Weights of the learned order's network as bfloat16 bit patterns:
+    hidden = relu(b1 + W1 x) (64 x 8), score = b2 + W2 . hidden; key_bits sets
+    the key resolution (key = floor(score * 2^key_bits))."""
+    w1: np.ndarray
+    b1: np.ndarray
+    w2: np.ndarray
+    b2: int
+    key_bits: int
+
+
+def _bf16_bits_truncated(a: np.ndarray) -> np.ndarray:
+    return (np.ascontiguousarray(a, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def random_model(seed: int, scale: float = 1.0, key_bits: int = 8) -> Model:
+    """Seeded random weights (normal, times `scale`, truncated to bfloat16)."""
+    rng = np.random.default_rng(seed)
+    w1 = _bf16_bits_truncated(rng.normal(size=(64, 8)) * scale)
+    b1 = _bf16_bits_truncated(rng.normal(size=64) * scale)
+    w2 = _bf16_bits_truncated(rng.normal(size=64) * scale)
+    b2 = int(_bf16_bits_truncated(rng.normal(size=1) * scale)[0])
+    return Model(w1, b1, w2, b2, key_bits)
+
+
+def zero_model(key_bits: int = 8) -> Model:
+    z = np.zeros(64, dtype=np.uint16)
+    return Model(np.zeros((64, 8), dtype=np.uint16), z.copy(), z.copy(), 0, key_bits)
+
+
+def initial_params(seed: int) -> np.ndarray:
+    """Seeded float32 starting point of training (641 values: W1 uniform in
+    +-1/sqrt(8), W2 uniform in +-1/8, biases 0)."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(641, dtype=np.float32)
+    p[:512] = rng.uniform(-1, 1, size=512) / np.sqrt(8.0)
+    p[576:640] = rng.uniform(-1, 1, size=64) / 8.0
+    return p
+
+
+def training_graphs(count: int = 4, first_seed: int = 100, sizes=(16384,)) -> list[Hypergraph]:
+    """Random SNN training graphs: node counts cycling through `sizes`,
+    hyperedge sizes uniform in 128..256, seeds first_seed, first_seed + 1, ..."""
+    return [random_snn(sizes[i % len(sizes)], 128, first_seed + i, size_max=256)
+            for i in range(count)]
