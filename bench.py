@@ -23,6 +23,7 @@ bounded sample of the workload family.  Multi-GPU: independent replicas
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -41,6 +42,33 @@ WORKLOAD = "random SNN hypergraph, 16,384 nodes, one hyperedge per node of 128 p
 SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same generator family "
                "(32 pins per hyperedge, 65,536 pins, Omega=128, Delta=512, seed 0); the 16k-node "
                "workload needs well over 10 minutes of oracle time on one core")
+
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel
+# (profiles/k_score_snn16k_level200.md: mean over the 435 launches of one
+# step), valid only while the kernel's sources are the ones captured.
+MEASURED_TRAFFIC = {
+    "k_score": (13478669.5, {
+        "paper_2604_14411_gb300/csrc/k_score.cuh":
+            "2035e5fdad658d655a0458e68da28453574fb45652b88d860d655fad64e555dc",
+        "paper_2604_14411_gb300/csrc/k_score.cu":
+            "baf3ac204b4f955a73960be99fa51bf122ccd656aa7b50d9c39f5b4f44e8ecad"}),
+}
+
+
+def measured_traffic(kernel):
+    entry = MEASURED_TRAFFIC.get(kernel)
+    if entry is None:
+        return None
+    value, files = entry
+    for rel, digest in files.items():
+        path = os.path.join(ROOT, rel)
+        if not os.path.exists(path):
+            return None
+        with open(path, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return value
 
 
 def load_peaks():
@@ -363,7 +391,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": {"kernel": f"{top} ({desc})", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(top),
                          "peak_kind": f"{peak_kind} (hbm copy)",
                          "launches": int(n_k), "avg_launch_us": 1000.0 * ms_k / max(n_k, 1),
                          "bytes_per_launch": bytes_k / max(n_k, 1),
