@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "coarsening pins/s and partition wall-time at equal λ−1 cost, plain vs learned"
 OMEGA, DELTA = 1 << 10, 1 << 12
 WORKLOAD = "random SNN hypergraph, 16,384 nodes, one hyperedge per node of 128 pins (src + 127 distinct targets), 2,097,152 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0"
+LEARN_TRAIN_GRAPHS, LEARN_PER_NODE, LEARN_STEPS, LEARN_BATCH, LEARN_LR, LEARN_KEY_BITS = \
+    4, 16, 2000, 4096, 3e-3, 6
 SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same generator family "
                "(32 pins per hyperedge, 65,536 pins, Omega=128, Delta=512, seed 0); the 16k-node "
                "workload needs well over 10 minutes of oracle time on one core")
@@ -243,6 +245,66 @@ def run_batch(args, rank, world):
         dist.destroy_process_group()
 
 
+def recount(g, ids, omega, delta):
+    """Cost (Eq. 1) and feasibility of a partition recounted on the host."""
+    off = g.offsets.astype(np.int64)
+    E = len(off) - 1
+    sizes = np.diff(off)
+    edge = np.repeat(np.arange(E, dtype=np.int64), sizes)
+    part = ids[g.pins].astype(np.int64)
+    K = int(ids.max()) + 1
+    lam = np.bincount(np.unique(edge * K + part) // K, minlength=E)
+    cost = int((lam - 1).sum())
+    weight = np.bincount(ids, minlength=K)
+    dst = np.ones(len(g.pins), dtype=bool)
+    dst[off[:-1]] = False                                  # first pin = source
+    inbound = np.bincount(np.unique(part[dst] * E + edge[dst]) // E, minlength=K)
+    return cost, bool(weight.max() <= omega and inbound.max() <= delta)
+
+
+def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
+    """Learned candidate order: train on seeded graphs of the same family
+    (untimed), then time partitions of the workload with the trained model."""
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    train = synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,))
+    model, losses = H.train_model(train, OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE,
+                                  steps=LEARN_STEPS, batch=LEARN_BATCH, lr=LEARN_LR,
+                                  key_bits=LEARN_KEY_BITS, init_params=synth.initial_params(0),
+                                  stream=stream)
+    train_s = time.perf_counter() - t0
+    step(model=model)
+    torch.cuda.synchronize()
+    times, stats, res = [], [], None
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, st = step(H.HGP_DEBUG_TIMING, model=model)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        stats.append(st)
+    ms = statistics.median(times)
+    ids = d_ids.cpu().numpy()
+    cost, feasible = recount(g, ids, OMEGA, DELTA)
+    return {"model": f"8-64-1 MLP, bfloat16 weights, key_bits {LEARN_KEY_BITS}",
+            "training": {"graphs": f"{LEARN_TRAIN_GRAPHS} random SNN hypergraphs, 16,384 nodes, "
+                                   "hyperedge size 128..256, seeds 100..", "labels": "co-location in "
+                                   "the plain partition", "pairs": LEARN_PER_NODE * 16384 * LEARN_TRAIN_GRAPHS,
+                         "steps": LEARN_STEPS, "batch": LEARN_BATCH, "seconds": train_s,
+                         "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean())},
+            "ms_per_step": ms, "pins_per_s": g.num_pins / (ms / 1000.0),
+            "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
+            "coarsening_pins_per_s": g.num_pins / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
+            "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
+            "cost_recounted": cost, "feasible": feasible,
+            "cost_ratio_vs_plain": res[0] / plain_cost, "time_ratio_vs_plain": ms / plain_ms,
+            "steps": len(times)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,6 +315,8 @@ def main():
     ap.add_argument("--workload", default="snn16k", choices=["snn16k", "batch64"],
                     help="snn16k: the default single-hypergraph workload; batch64: 64 uneven "
                          "hypergraphs through hgp_partition_batch (prints its own JSON line)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-order leg (training + timed learned partitions)")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run exactly one step, exit (for ncu launch lists)")
     args = ap.parse_args()
@@ -289,10 +353,10 @@ def main():
     d_pin = torch.empty(N, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
-    def step(debug=0):
+    def step(debug=0, model=None):
         h = H.hgp_create(N, d_off, d_pins, stream=stream)
         try:
-            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug)
+            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug, 0, model)
             st = H.hgp_get_stats(h)
         finally:
             H.hgp_destroy(h)
@@ -356,6 +420,10 @@ def main():
     h2d = g.offsets.nbytes + g.pins.nbytes
     d2h = h_ids.numel() * 4 + nparts * 8 + nparts * 4 + 8 + 4
 
+    learned = None
+    if not args.no_learned:
+        learned = learned_leg(args, step, flush, stream, g, d_ids, res[0], statistics.median(times), H)
+
     st = stats[-1]
     peak, peak_kind = load_peaks()
     # roofline of the kernel with the largest summed device time in the timed steps
@@ -399,6 +467,8 @@ def main():
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kern.items()},
             "clocks": clocks,
         }
+        if learned is not None:
+            line["learned"] = learned
         if not args.no_cpu_baseline:
             v, ts = oracle_sample(steps=3)
             line["cpu_baseline"] = {"value": v, "unit": "pins/s", "cores": 1, "kind": "oracle",

@@ -96,13 +96,45 @@ int hgp_create(int32_t num_nodes, int32_t num_edges,
                const int32_t *node_weights, const int32_t *edge_weights,
                uint32_t flags, void *stream, hgp_graph **out);
 
+/*
+ * Learned candidate order (an extension; the paper has no counterpart).
+ * A two-layer network scores each pair (n, m) from 8 features, symmetric in
+ * n and m, each passed through lg1p(x) = k + (1 + x - 2^k) / 2^k for
+ * 2^k <= 1 + x < 2^(k+1) (log2(1 + x) with a linear mantissa):
+ *   x0 hist(n,m) (Eq. (2))          x1 |in(n) u in(m)|
+ *   x2, x3 min, max of |I(n)|, |I(m)|   x4, x5 min, max of |in(n)|, |in(m)|
+ *   x6, x7 min, max of w(n), w(m)
+ *   h_j = relu(b1_j + sum_i W1_ji x_i) (j < 64),  s = b2 + sum_j W2_j h_j,
+ *   key = floor(s * 2^key_bits) clamped to [-2^30, 2^30].
+ * Weights are bfloat16 bit patterns widened exactly to float32; each sum is
+ * a chain of fused multiply-adds in index order (h_j over i, then s over j,
+ * folding in each h_j as it is computed), which makes the keys
+ * reproducible bit for bit.  pair(n) is the valid m (the same Omega and
+ * Delta checks as Sec. III-B.2) with the largest (key, hist, id); matching
+ * compares (key, hist) then id.  A model whose weights are all zero gives
+ * the plain order exactly.
+ */
+#define HGP_MLP_IN 8
+#define HGP_MLP_HIDDEN 64
+#define HGP_MLP_PARAMS 641         /* W1 (64 x 8), b1 (64), W2 (64), b2 */
+typedef struct {
+    uint16_t w1[HGP_MLP_HIDDEN * HGP_MLP_IN];   /* W1[j][i] at 8 j + i */
+    uint16_t b1[HGP_MLP_HIDDEN];
+    uint16_t w2[HGP_MLP_HIDDEN];
+    uint16_t b2;
+    int16_t key_bits;          /* 0..20 */
+    int32_t reserved[3];       /* must be zero */
+} hgp_model;
+
 typedef struct {
     int32_t refine_passes;     /* refinement passes per level (default 1; 0 = none) */
     uint32_t debug;            /* HGP_DEBUG_* bits */
     int32_t max_levels;        /* > 0: stop coarsening after this many matchings, the clusters
                                   of the last one becoming the parts (as when the node target
                                   is reached); 0 = the paper's stop rule only */
-    int32_t reserved[5];       /* must be zero */
+    int32_t reserved[3];       /* must be zero */
+    const hgp_model *model;    /* NULL: the paper's Eq. (2) order; else the learned order
+                                  (host memory, read during the call) */
 } hgp_options;
 
 typedef struct {
@@ -184,12 +216,57 @@ enum {
     HGP_LEVEL_RHO_IN = 4,      /* [V_l] partition entering refinement */
     HGP_LEVEL_RHO_OUT = 5,     /* [V_l] partition after refinement */
     HGP_LEVEL_WEIGHT = 6,      /* [V_l] node weights */
-    HGP_LEVEL_REFINE = 7       /* [3] proposed moves, applied prefix, gain (as int64) */
+    HGP_LEVEL_REFINE = 7,      /* [3] proposed moves, applied prefix, gain (as int64) */
+    HGP_LEVEL_KEY = 8          /* [V_l] learned order only: key(n, pair(n)), 0 when none */
 };
 /* Length of array `which` of level l (-1 if absent). */
 int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which);
 /* Copies array `which` of level l into host buffer out (int64 elements). */
 int hgp_get_level_array(const hgp_graph *g, int32_t level, int32_t which, int64_t *out);
+
+/*
+ * Training pairs for the learned order, labelled by a partition of the
+ * handle's input (typically the plain method's result).  Slot
+ * s = n * per_node + k (k < per_node) draws u0, u1 = outputs 2s and 2s + 1 of
+ * SplitMix64 started at `seed`, takes e = the (u0 mod |I(n)|)-th hyperedge of
+ * I(n) (ascending ids) and m = the (u1 mod |pins(e)|)-th pin of e in the
+ * input's pin order, and stores the 8 features of (n, m) (as above) in
+ * x[8 s .. 8 s + 8), the label [part_ids[n] == part_ids[m]] in y[s] and m in
+ * partner[s]; when m = n or I(n) is empty the slot holds zeros, y = -1 and
+ * partner = -1.  All arrays are device memory: part_ids [num_nodes], x
+ * [num_nodes * per_node * 8] float, y [num_nodes * per_node] float,
+ * partner [num_nodes * per_node] int32 or NULL.  Runs on the handle's
+ * stream; the outputs are complete when it reaches the end of the call.
+ */
+int hgp_learn_samples(hgp_graph *g, const int32_t *part_ids, uint64_t seed, int32_t per_node,
+                      float *x, float *y, int32_t *partner);
+
+typedef struct {
+    int32_t steps;             /* Adam steps */
+    int32_t batch;             /* samples per step: step k uses samples k*batch .. k*batch +
+                                  batch - 1, modulo count (labels < 0 are skipped) */
+    float lr, beta1, beta2, eps;   /* Adam (Kingma and Ba, 2015) */
+    int32_t first_step;        /* Adam step number t of the first step (>= 1) */
+    int32_t reserved[3];       /* must be zero */
+} hgp_train_options;
+
+/*
+ * Minibatch training of the learned order's network on the logistic loss
+ * log(1 + e^s) - y s.  The forward pass uses the parameters rounded to
+ * bfloat16 (nearest even) with float32 arithmetic; the gradient (ReLU
+ * derivative 1 where the pre-activation is > 0) updates the float32 master
+ * copy.  x [count * 8] and y [count] are device memory; params
+ * [HGP_MLP_PARAMS] (W1 at 8 j + i, b1 at 512 + j, W2 at 576 + j, b2 at 640)
+ * and adam [2 * HGP_MLP_PARAMS] (first then second moments) are host memory,
+ * read and updated; loss (host, [steps] or NULL) receives each step's mean
+ * batch loss before its update.  Deterministic: partial sums are added in a
+ * fixed order.  Synchronous on `stream`.
+ */
+int hgp_train_mlp(const float *x, const float *y, int64_t count, const hgp_train_options *opt,
+                  float *params, float *adam, float *loss, void *stream);
+
+/* Model from float32 master parameters (round to nearest even bfloat16). */
+int hgp_model_from_params(const float *params, int32_t key_bits, hgp_model *out);
 
 const char *hgp_error_string(int status);
 const char *hgp_last_error(const hgp_graph *g);

@@ -88,6 +88,8 @@ def _load():
             lib.oracle_mlp.argtypes = [vp, vp, vp, u16, i32, vp, vp, vp]
             lib.orun_features0.argtypes = [vp, i32, i32, vp]
             lib.orun_learn_samples.argtypes = [vp, vp, u64, i32, vp, vp, vp]
+            lib.orun_score0_learned_nodes.argtypes = [vp, i64, i64, vp, vp, vp, u16, i32, vp, i32,
+                                                      vp, vp, vp]
             lib.oracle_splitmix64_at.argtypes = [u64, u64]
             lib.oracle_splitmix64_at.restype = u64
             lib.oracle_train_step.argtypes = [vp, vp, vp, i64, f64, f64, f64, f64, i32, vp, vp,
@@ -176,6 +178,18 @@ class Run:
         inb = np.empty(max(np_, 1), dtype=np.int32)
         lib.orun_part_stats(self._h, _p(w), _p(inb))
         return Result(ids, int(lib.orun_cost(self._h)), int(np_), w[:np_], inb[:np_])
+
+    def score0_learned_nodes(self, omega, delta, model, nodes):
+        """Learned-order (pair, score, key) of the listed level-0 nodes only."""
+        w1, b1, w2 = _model_arrays(model)
+        nodes = _i32(nodes)
+        out = [np.empty(len(nodes), dtype=np.int32) for _ in range(3)]
+        rc = _load().orun_score0_learned_nodes(self._h, int(omega), int(delta), _p(w1), _p(b1), _p(w2),
+                                               int(model.b2), int(model.key_bits), _p(nodes), len(nodes),
+                                               *[_p(o) for o in out])
+        if rc:
+            raise OracleError(rc, "score0_learned_nodes")
+        return tuple(out)
 
     def features0(self, n, m):
         x = np.empty(8, dtype=np.float32)

@@ -1453,3 +1453,26 @@ int oracle_train_step(const float *p, const float *x, const float *y, int64_t co
 }
 
 uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
+
+/* Learned-order candidate of the listed level-0 nodes only (pair[t], score[t],
+ * key[t] belong to nodes[t]). */
+int orun_score0_learned_nodes(const orun *r, int64_t omega, int64_t delta, const uint16_t *w1,
+                              const uint16_t *b1, const uint16_t *w2, uint16_t b2, int32_t key_bits,
+                              const int32_t *nodes, int32_t count, int32_t *pair, int32_t *score,
+                              int32_t *key) {
+    const olevel *g = &r->G[0];
+    omodel M;
+    int rc = model_from_bits(w1, b1, w2, b2, key_bits, &M);
+    if (rc) return rc;
+    for (int32_t t = 0; t < count; ++t) if (nodes[t] < 0 || nodes[t] >= g->V) return ORC_INVALID;
+    int64_t *hist = (int64_t *)calloc((size_t)g->V, sizeof(int64_t));
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->V);
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!hist || !touched || !stamp) { free(hist); free(touched); free(stamp); return ORC_OOM; }
+    for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
+    for (int32_t t = 0; t < count; ++t)
+        score_node_learned(g, r->ew, omega, delta, &M, nodes[t], pair + t, score + t, key + t, hist,
+                           touched, stamp);
+    free(hist); free(touched); free(stamp);
+    return ORC_OK;
+}

@@ -14,9 +14,17 @@ namespace hgp {
 cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
                       int32_t *pair, int32_t *score, int32_t *status,
                       unsigned long long *bytes, uint32_t debug, cudaStream_t s);
+cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
+                              int64_t delta, const hgp_model *model, int32_t *pair,
+                              int32_t *score, int32_t *key, int32_t *status,
+                              unsigned long long *bytes, uint32_t debug, cudaStream_t s);
+bool model_valid(const hgp_model *m);
+cudaError_t run_learn_samples(const Level &L0, const int32_t *ew, const int32_t *part_ids,
+                              uint64_t seed, int32_t per_node, float *x, float *y,
+                              int32_t *partner, cudaStream_t s);
 cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
-                      int32_t *match, int32_t *gamma, int32_t *d_V2, int32_t *status,
-                      cudaStream_t s);
+                      const int32_t *key, int32_t *match, int32_t *gamma, int32_t *d_V2,
+                      int32_t *status, cudaStream_t s);
 cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
                          const int32_t *pair, const int32_t *score, int32_t *status,
                          cudaStream_t s);
@@ -68,7 +76,7 @@ struct hgp_graph {
     int32_t max_w = 0, max_in = 0;
     std::string err;
     hgp_stats stats{};
-    std::vector<std::vector<int64_t>> dbg[8];
+    std::vector<std::vector<int64_t>> dbg[9];
 };
 
 static int fail(hgp_graph *g, int code, const std::string &msg) {
@@ -263,10 +271,13 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     int32_t passes = 1;
     uint32_t debug = 0;
     int32_t max_levels = 0;
+    const hgp_model *model = nullptr;
     if (opt) {
         if (opt->refine_passes < 0) return fail(g, HGP_ERR_INVALID_ARG, "refine_passes must be >= 0");
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 3; ++i)
             if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->model && !model_valid(opt->model))
+            return fail(g, HGP_ERR_INVALID_ARG, "model: key_bits must be in 0..20 and reserved zero");
         if (opt->max_levels < 0) return fail(g, HGP_ERR_INVALID_ARG, "max_levels must be >= 0");
         max_levels = opt->max_levels;
         if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
@@ -274,6 +285,7 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
             return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
         passes = opt->refine_passes;
         debug = opt->debug;
+        model = opt->model;
     }
     if (g->max_w > omega || g->max_in > delta)
         return fail(g, HGP_ERR_INFEASIBLE, "a single node exceeds omega or delta; no partition exists");
@@ -325,17 +337,22 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         for (;;) {
             Level &L = levels.back();
             int l = (int)levels.size() - 1;
-            int32_t *pair, *score;
+            int32_t *pair, *score, *key = nullptr;
             CKP(dalloc(tmp, &pair, L.V), "alloc pair");
             CKP(dalloc(tmp, &score, L.V), "alloc score");
+            if (model) CKP(dalloc(tmp, &key, L.V), "alloc key");
             CKP(dalloc(lv, &L.match, L.V), "alloc match");
             CKP(dalloc(lv, &L.gamma, L.V), "alloc gamma");
             tm.start(0, &ev_a);
-            CKP(run_score(tmp, L, g->ew, omega, delta, pair, score, d_status,
-                          tm.on ? d_bytes : nullptr, debug, s), "score");
+            if (model)
+                CKP(run_score_learned(tmp, L, g->ew, omega, delta, model, pair, score, key, d_status,
+                                      tm.on ? d_bytes : nullptr, debug, s), "score");
+            else
+                CKP(run_score(tmp, L, g->ew, omega, delta, pair, score, d_status,
+                              tm.on ? d_bytes : nullptr, debug, s), "score");
             tm.stop(0, ev_a);
             tm.start(1, &ev_a);
-            CKP(run_match(tmp, L.V, pair, score, L.match, L.gamma, d_V2, d_status, s), "match");
+            CKP(run_match(tmp, L.V, pair, score, key, L.match, L.gamma, d_V2, d_status, s), "match");
             tm.stop(1, ev_a);
             int32_t h[2];
             CKP(cudaMemcpyAsync(&h[0], d_V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read V2");
@@ -349,6 +366,7 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
             if (debug & HGP_DEBUG_KEEP_LEVELS) {
                 keep_array(g, HGP_LEVEL_PAIR, l, pair, L.V, s);
                 keep_array(g, HGP_LEVEL_SCORE, l, score, L.V, s);
+                if (key) keep_array(g, HGP_LEVEL_KEY, l, key, L.V, s);
                 keep_array(g, HGP_LEVEL_MATCH, l, L.match, L.V, s);
                 keep_array(g, HGP_LEVEL_WEIGHT, l, L.w, L.V, s);
             }
@@ -572,7 +590,7 @@ extern "C" int hgp_get_stats(const hgp_graph *g, hgp_stats *st) {
 }
 
 extern "C" int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which) {
-    if (!g || which < 0 || which > 7 || level < 0) return -1;
+    if (!g || which < 0 || which > HGP_LEVEL_KEY || level < 0) return -1;
     const auto &vv = g->dbg[which];
     if (level >= (int)vv.size() || (vv[level].empty() && which != HGP_LEVEL_REFINE)) return -1;
     return (int64_t)vv[level].size();
@@ -583,6 +601,18 @@ extern "C" int hgp_get_level_array(const hgp_graph *g, int32_t level, int32_t wh
     if (n < 0 || !out) return HGP_ERR_INVALID_ARG;
     const auto &v = g->dbg[which][level];
     for (int64_t i = 0; i < n; ++i) out[i] = v[i];
+    return HGP_OK;
+}
+
+extern "C" int hgp_learn_samples(hgp_graph *g, const int32_t *part_ids, uint64_t seed,
+                                 int32_t per_node, float *x, float *y, int32_t *partner) {
+    if (!g) return HGP_ERR_INVALID_ARG;
+    if (!part_ids || !x || !y || per_node < 1)
+        return fail(g, HGP_ERR_INVALID_ARG, "part_ids, x, y are required and per_node must be >= 1");
+    if ((int64_t)g->N * per_node > ((int64_t)1 << 40))
+        return fail(g, HGP_ERR_INVALID_ARG, "num_nodes * per_node too large");
+    cudaError_t e = run_learn_samples(g->L0, g->ew, part_ids, seed, per_node, x, y, partner, g->stream);
+    if (e) return cuda_fail(g, e, "learn_samples");
     return HGP_OK;
 }
 

@@ -1,0 +1,643 @@
+// Learned candidate order: a two-layer network ranks the candidates of a node
+// before Eq. (2)'s hist (an extension of Sec. III-A; the paper has none).
+//
+//   x     = 8 features of the pair (n, m), symmetric in n and m:
+//           lg1p of hist(n,m), |in(n) u in(m)|, min/max |I|, min/max |in|,
+//           min/max w, where lg1p(x) = k + (1 + x - 2^k) / 2^k for
+//           2^k <= 1 + x < 2^(k+1) (log2(1 + x) with a linear mantissa)
+//   h_j   = relu(b1_j + sum_i W1_ji x_i), s = b2 + sum_j W2_j h_j
+//   key   = floor(s * 2^key_bits), clamped to [-2^30, 2^30]
+//   pair(n) = the valid m with the largest (key, hist, id)
+// Weights are bfloat16, widened exactly to float; every sum is a chain of
+// fused multiply-adds in index order (h_j over i, then s over j with each
+// h_j folded in as soon as it is computed).  That order is part of the
+// definition, so the keys are bit-identical to any other implementation
+// that follows it.  The weights travel in the kernel's parameter space, so
+// every FMA takes its weight from the constant bank.
+//
+// Scoring kernel: one 1024-thread CTA per node.  Pass 1 accumulates, per
+// neighbour m, hist(n, m) and inter(n, m) = |in(n) n in(m)| (a hyperedge e
+// of I(n) is in in(x) for every pin x except its source, unless the source's
+// node also holds a destination of e); |in(n) u in(m)| = |in(n)| + |in(m)| -
+// inter(n, m), so the Delta check needs no per-pair set union.  Pass 2
+// evaluates the network for every valid neighbour and reduces (key, hist,
+// id) over the CTA.  Histograms: two dense shared-memory arrays when the
+// level fits on chip, otherwise per-CTA open-addressing tables in global
+// memory.
+//
+// Training kernels: features and co-location labels of sampled pairs, and
+// minibatch Adam steps on the logistic loss with the forward pass in
+// bfloat16 weights and float32 arithmetic; per-warp partial gradients are
+// summed in a fixed order, so training is deterministic.
+#include <cstring>
+
+#include "hgp_internal.cuh"
+
+namespace hgp {
+
+constexpr int kMlpIn = HGP_MLP_IN;
+constexpr int kMlpHid = HGP_MLP_HIDDEN;
+constexpr int kMlpParams = HGP_MLP_PARAMS;
+constexpr int kLearnThreads = 1024;
+constexpr int kLearnWarps = kLearnThreads / 32;
+constexpr int32_t kKeyBias = 1 << 30;
+
+struct MlpParams {
+    float w1[kMlpHid * kMlpIn];
+    float b1[kMlpHid];
+    float w2[kMlpHid];
+    float b2;
+    int32_t key_bits;
+};
+
+struct LearnedArgs {
+    int32_t V, E;
+    const int32_t *w, *poff, *pins, *ioff, *inc, *noff, *ew, *src;
+    const uint8_t *sdst, *dead;
+    int64_t omega, delta;
+    int32_t *pair, *score, *key;
+    int32_t *next, *status;
+    int32_t *gkeys, *gvals, *ginter;
+    int32_t gcap;
+    unsigned long long *bytes;
+};
+
+__device__ __forceinline__ float pow2_exact(int k) {       // 2^k, -126 <= k <= 127
+    return __int_as_float((127 + k) << 23);
+}
+
+__device__ __forceinline__ float lg1p_dev(int64_t x) {
+    unsigned long long y = (unsigned long long)x + 1ull;
+    int k = 63 - __clzll((long long)y);
+    float frac = __fmul_rn(__ull2float_rn(y - (1ull << k)), pow2_exact(-k));
+    return __fadd_rn((float)k, frac);
+}
+
+__device__ __forceinline__ float mlp_eval(const MlpParams &M, const float *x) {
+    float s = M.b2;
+#pragma unroll
+    for (int j = 0; j < kMlpHid; ++j) {
+        float h = M.b1[j];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) h = __fmaf_rn(M.w1[j * kMlpIn + i], x[i], h);
+        h = h > 0.0f ? h : 0.0f;
+        s = __fmaf_rn(M.w2[j], h, s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ int32_t key_of(float s, int32_t key_bits) {
+    float q = floorf(__fmul_rn(s, pow2_exact(key_bits)));
+    if (!(q > -1073741824.0f)) return -kKeyBias;
+    if (q > 1073741824.0f) return kKeyBias;
+    return (int32_t)q;
+}
+
+__device__ __forceinline__ unsigned long long composite(int32_t key, int32_t hist) {
+    return ((unsigned long long)(uint32_t)(key + kKeyBias) << 32) | (uint32_t)hist;
+}
+
+__device__ __forceinline__ void features(const LearnedArgs &a, int32_t n, int32_t m, int32_t hist,
+                                         int64_t uni, int64_t in_n, int64_t in_m, float *x) {
+    int64_t dn = a.ioff[n + 1] - a.ioff[n], dm = a.ioff[m + 1] - a.ioff[m];
+    int64_t wn = a.w[n], wm = a.w[m];
+    x[0] = lg1p_dev(hist);
+    x[1] = lg1p_dev(uni);
+    x[2] = lg1p_dev(min(dn, dm));
+    x[3] = lg1p_dev(max(dn, dm));
+    x[4] = lg1p_dev(min(in_n, in_m));
+    x[5] = lg1p_dev(max(in_n, in_m));
+    x[6] = lg1p_dev(min(wn, wm));
+    x[7] = lg1p_dev(max(wn, wm));
+}
+
+// (comp, id) lexicographic maximum over the CTA; every thread gets it.
+__device__ void block_argmax(unsigned long long &comp, int32_t &id, unsigned long long *s_c,
+                             int32_t *s_i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long c2 = __shfl_xor_sync(0xffffffffu, comp, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, id, o);
+        if (c2 > comp || (c2 == comp && i2 > id)) { comp = c2; id = i2; }
+    }
+    __syncthreads();
+    if (lane_id() == 0) { s_c[warp_id()] = comp; s_i[warp_id()] = id; }
+    __syncthreads();
+    comp = s_c[0];
+    id = s_i[0];
+    for (int w = 1; w < kLearnWarps; ++w)
+        if (s_c[w] > comp || (s_c[w] == comp && s_i[w] > id)) { comp = s_c[w]; id = s_i[w]; }
+}
+
+__device__ __forceinline__ uint32_t hash_node(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kLearnThreads)
+k_score_learned(LearnedArgs a, MlpParams M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);
+    int32_t *inter = hist + (DENSE ? a.V : 0);
+    __shared__ unsigned long long s_c[kLearnWarps];
+    __shared__ int32_t s_i[kLearnWarps];
+    __shared__ int32_t s_n;
+    int32_t *gk = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
+    int32_t *gv = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
+    int32_t *gi = DENSE ? nullptr : a.ginter + (int64_t)blockIdx.x * a.gcap;
+    const int32_t cap = DENSE ? a.V : a.gcap;
+    const uint32_t mask = (uint32_t)a.gcap - 1u;
+    unsigned long long bytes = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int32_t n = s_n;
+        if (n >= a.V) break;
+        if (a.dead && a.dead[n]) {              // no valid candidate can exist
+            if (threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; a.key[n] = 0; }
+            __syncthreads();
+            continue;
+        }
+        for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
+            if (DENSE) { hist[i] = 0; inter[i] = 0; }
+            else { gk[i] = -1; gv[i] = 0; gi[i] = 0; }
+        }
+        __syncthreads();
+        // ---- pass 1: hist(n, .) and inter(n, .) ----
+        const int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
+        const int32_t mine = (i1 - i0 - warp_id() + kLearnWarps - 1) / kLearnWarps;
+        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
+            int32_t we = 0, p0 = 0, p1 = 0, se = -1, sd = 0;
+            if (r0 + lane_id() < mine) {
+                int32_t e = a.inc[i0 + warp_id() + kLearnWarps * (r0 + lane_id())];
+                we = a.ew[e];
+                p0 = a.poff[e];
+                p1 = a.poff[e + 1];
+                se = a.src[e];
+                sd = a.sdst[e];
+            }
+            const int32_t cnt = min(32, mine - r0);
+            for (int32_t t = 0; t < cnt; ++t) {
+                const int32_t wt = __shfl_sync(0xffffffffu, we, t);
+                const int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
+                const int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
+                const int32_t s_e = __shfl_sync(0xffffffffu, se, t);
+                const int32_t sd_e = __shfl_sync(0xffffffffu, sd, t);
+                const bool n_in = s_e != n || sd_e;     // e in in(n)
+                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
+                    const int32_t m = a.pins[j];
+                    if (m == n) continue;
+                    const int32_t both = (n_in && (m != s_e || sd_e)) ? 1 : 0;
+                    if (DENSE) {
+                        atomicAdd(&hist[m], wt);
+                        if (both) atomicAdd(&inter[m], 1);
+                    } else {
+                        uint32_t slot = hash_node((uint32_t)m) & mask;
+                        for (int32_t probes = 0;; ++probes) {
+                            int32_t kk = atomicCAS(&gk[slot], -1, m);
+                            if (kk == -1 || kk == m) {
+                                atomicAdd(&gv[slot], wt);
+                                if (both) atomicAdd(&gi[slot], 1);
+                                break;
+                            }
+                            slot = (slot + 1) & mask;
+                            if (probes + 1 >= a.gcap) { set_status(a.status, kDevLimit); break; }
+                        }
+                    }
+                }
+                if (lane_id() == 0) bytes += 24ull + 4ull * (unsigned long long)(b1 - b0);
+            }
+        }
+        __syncthreads();
+        // ---- pass 2: the network on every valid neighbour ----
+        const int64_t in_n = a.noff[n + 1] - a.noff[n];
+        const int64_t wn = a.w[n];
+        unsigned long long best_c = 0ull;
+        int32_t best_m = -1;
+        for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
+            int32_t m, h, it;
+            if (DENSE) { m = i; h = hist[i]; it = inter[i]; }
+            else { m = gk[i]; h = m >= 0 ? gv[i] : 0; it = m >= 0 ? gi[i] : 0; }
+            if (h == 0) continue;
+            if (a.dead && a.dead[m]) continue;
+            if (wn + a.w[m] > a.omega) continue;
+            const int64_t in_m = a.noff[m + 1] - a.noff[m];
+            const int64_t uni = in_n + in_m - it;
+            if (uni > a.delta) continue;
+            float x[kMlpIn];
+            features(a, n, m, h, uni, in_n, in_m, x);
+            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
+            const unsigned long long c = composite(k, h);
+            if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
+            bytes += 20ull;
+        }
+        block_argmax(best_c, best_m, s_c, s_i);
+        if (threadIdx.x == 0) {
+            a.pair[n] = best_m;
+            a.score[n] = best_m >= 0 ? (int32_t)(best_c & 0xffffffffull) : 0;
+            a.key[n] = best_m >= 0 ? (int32_t)(best_c >> 32) - kKeyBias : 0;
+            bytes += 24ull;
+        }
+        __syncthreads();
+    }
+    if (a.bytes) {
+        bytes = warp_sum(bytes);
+        if (lane_id() == 0 && bytes) atomicAdd(a.bytes, bytes);
+    }
+}
+
+static __global__ void k_max_visits(int32_t V, const int32_t *ioff, const int32_t *inc,
+                                    const int32_t *poff, unsigned long long *out) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        unsigned long long s = 0;
+        for (int32_t k = ioff[n] + lane_id(); k < ioff[n + 1]; k += 32) {
+            int32_t e = inc[k];
+            s += (unsigned long long)(poff[e + 1] - poff[e]);
+        }
+        s = warp_sum(s);
+        if (lane_id() == 0) atomicMax(out, s);
+    }
+}
+
+// Host copy of a model's weights, widened from bfloat16 (exact).
+static float bf16_bits_to_float(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
+bool model_valid(const hgp_model *m) {
+    if (m->key_bits < 0 || m->key_bits > 20) return false;
+    for (int i = 0; i < 3; ++i)
+        if (m->reserved[i]) return false;
+    return true;
+}
+
+static MlpParams widen(const hgp_model *m) {
+    MlpParams P;
+    for (int q = 0; q < kMlpHid * kMlpIn; ++q) P.w1[q] = bf16_bits_to_float(m->w1[q]);
+    for (int j = 0; j < kMlpHid; ++j) {
+        P.b1[j] = bf16_bits_to_float(m->b1[j]);
+        P.w2[j] = bf16_bits_to_float(m->w2[j]);
+    }
+    P.b2 = bf16_bits_to_float(m->b2);
+    P.key_bits = m->key_bits;
+    return P;
+}
+
+cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
+                              int64_t delta, const hgp_model *model, int32_t *pair,
+                              int32_t *score, int32_t *key, int32_t *status,
+                              unsigned long long *bytes, uint32_t debug, cudaStream_t s) {
+    if (L.V <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    LearnedArgs a{};
+    a.V = L.V; a.E = L.E;
+    a.w = L.w; a.poff = L.poff; a.pins = L.pins; a.ioff = L.ioff; a.inc = L.inc;
+    a.noff = L.noff; a.ew = ew; a.src = L.src; a.sdst = L.sdst; a.dead = L.dead;
+    a.omega = omega; a.delta = delta;
+    a.pair = pair; a.score = score; a.key = key; a.status = status; a.bytes = bytes;
+    const MlpParams M = widen(model);
+    cudaError_t e = dalloc(ar, &a.next, 1);
+    if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
+    if (e) return e;
+    const int sms = num_sms();
+    const size_t dense_smem = 2 * sizeof(int32_t) * (size_t)L.V;
+    if (dense_smem + 4096 <= (size_t)max_smem &&
+        !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER))) {
+        e = allow_dynamic_smem(k_score_learned<true>);
+        if (e) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_learned<true>, kLearnThreads,
+                                                      dense_smem);
+        if (per_sm < 1) per_sm = 1;
+        int blocks = sms * per_sm;
+        if (blocks > L.V) blocks = L.V;
+        k_score_learned<true><<<blocks, kLearnThreads, dense_smem, s>>>(a, M);
+        count_launch();
+        return cudaGetLastError();
+    }
+    unsigned long long *d_work = nullptr;
+    e = dalloc(ar, &d_work, 1);
+    if (!e) e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), s);
+    if (e) return e;
+    k_max_visits<<<sms * 8, 256, 0, s>>>(L.V, L.ioff, L.inc, L.poff, d_work);
+    count_launch();
+    unsigned long long h_work = 0;
+    e = cudaMemcpyAsync(&h_work, d_work, sizeof(h_work), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return e;
+    unsigned long long distinct = h_work < (unsigned long long)L.V ? h_work : (unsigned long long)L.V;
+    unsigned long long gcap = 64;
+    while (gcap < 2 * distinct) gcap <<= 1;
+    if (gcap > (1ull << 30)) return cudaErrorMemoryAllocation;
+    a.gcap = (int32_t)gcap;
+    int blocks = sms * 2;
+    if (blocks > L.V) blocks = L.V;
+    e = dalloc(ar, &a.gkeys, (size_t)blocks * gcap);
+    if (!e) e = dalloc(ar, &a.gvals, (size_t)blocks * gcap);
+    if (!e) e = dalloc(ar, &a.ginter, (size_t)blocks * gcap);
+    if (e) return e;
+    k_score_learned<false><<<blocks, kLearnThreads, 0, s>>>(a, M);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- matching
+// best(m) over the children of m by (key, hist, id): the largest composite
+// (key, hist) first, then the largest id among the children holding it.
+__global__ void k_best_key(int32_t V, const int32_t *pair, const int32_t *score,
+                           const int32_t *key, unsigned long long *bkey) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = pair[n];
+        if (m >= 0) atomicMax(&bkey[m], composite(key[n], score[n]));
+    }
+}
+
+__global__ void k_best_id(int32_t V, const int32_t *pair, const int32_t *score, const int32_t *key,
+                          const unsigned long long *bkey, unsigned long long *best) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = pair[n];
+        if (m >= 0 && composite(key[n], score[n]) == bkey[m])
+            atomicMax(&best[m], (1ull << 32) | (uint32_t)n);
+    }
+}
+
+// ---------------------------------------------------------------- training data
+// The i-th output of SplitMix64 started at `seed` (Steele, Lea and Flood,
+// 2014): golden-ratio increment, then two xor-shift-multiply rounds and a
+// final xor-shift.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                            unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// |A n B| of two ascending lists, and the summed weight of the common items.
+__device__ __forceinline__ void intersect(const int32_t *A, int32_t a0, int32_t a1, const int32_t *B,
+                                          int32_t b0, int32_t b1, const int32_t *wt, int64_t *cnt,
+                                          int64_t *wsum) {
+    int64_t c = 0, s = 0;
+    while (a0 < a1 && b0 < b1) {
+        int32_t x = A[a0], y = B[b0];
+        if (x < y) ++a0;
+        else if (x > y) ++b0;
+        else { ++c; if (wt) s += wt[x]; ++a0; ++b0; }
+    }
+    *cnt = c;
+    *wsum = s;
+}
+
+// Slot s = n * per_node + k: e = I(n)[u0 mod |I(n)|], m = pins(e)[u1 mod |e|]
+// (input pin order), u0/u1 = outputs 2s and 2s + 1 of SplitMix64(seed).
+__global__ void k_learn_samples(int32_t N, int32_t per_node, unsigned long long seed,
+                                const int32_t *part, const int32_t *w, const int32_t *poff,
+                                const int32_t *pins, const int32_t *ioff, const int32_t *inc,
+                                const int32_t *noff, const int32_t *inn, const int32_t *ew,
+                                float *x, float *y, int32_t *partner) {
+    const int64_t S = (int64_t)N * per_node;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = (int32_t)(s / per_node);
+        const int32_t deg = ioff[n + 1] - ioff[n];
+        int32_t m = n;
+        if (deg > 0) {
+            unsigned long long u0 = splitmix64_at(seed, 2ull * (unsigned long long)s);
+            unsigned long long u1 = splitmix64_at(seed, 2ull * (unsigned long long)s + 1ull);
+            int32_t e = inc[ioff[n] + (int32_t)(u0 % (unsigned long long)deg)];
+            int32_t sz = poff[e + 1] - poff[e];
+            m = pins[poff[e] + (int32_t)(u1 % (unsigned long long)sz)];
+        }
+        float *xs = x + s * kMlpIn;
+        if (m == n) {
+            for (int i = 0; i < kMlpIn; ++i) xs[i] = 0.0f;
+            y[s] = -1.0f;
+            if (partner) partner[s] = -1;
+            continue;
+        }
+        int64_t shared = 0, hist = 0, inter = 0, dummy = 0;
+        intersect(inc, ioff[n], ioff[n + 1], inc, ioff[m], ioff[m + 1], ew, &shared, &hist);
+        intersect(inn, noff[n], noff[n + 1], inn, noff[m], noff[m + 1], nullptr, &inter, &dummy);
+        const int64_t in_n = noff[n + 1] - noff[n], in_m = noff[m + 1] - noff[m];
+        const int64_t dn = deg, dm = ioff[m + 1] - ioff[m];
+        const int64_t wn = w[n], wm = w[m];
+        xs[0] = lg1p_dev(hist);
+        xs[1] = lg1p_dev(in_n + in_m - inter);
+        xs[2] = lg1p_dev(min(dn, dm));
+        xs[3] = lg1p_dev(max(dn, dm));
+        xs[4] = lg1p_dev(min(in_n, in_m));
+        xs[5] = lg1p_dev(max(in_n, in_m));
+        xs[6] = lg1p_dev(min(wn, wm));
+        xs[7] = lg1p_dev(max(wn, wm));
+        y[s] = part[n] == part[m] ? 1.0f : 0.0f;
+        if (partner) partner[s] = m;
+    }
+}
+
+cudaError_t run_learn_samples(const Level &L0, const int32_t *ew, const int32_t *part_ids,
+                              uint64_t seed, int32_t per_node, float *x, float *y,
+                              int32_t *partner, cudaStream_t s) {
+    int64_t S = (int64_t)L0.V * per_node;
+    int blocks = div_up(S, 256);
+    if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+    if (blocks < 1) blocks = 1;
+    k_learn_samples<<<blocks, 256, 0, s>>>(L0.V, per_node, seed, part_ids, L0.w, L0.poff, L0.pins,
+                                           L0.ioff, L0.inc, L0.noff, L0.inn, ew, x, y, partner);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- training
+constexpr int kTrainThreads = 256;
+constexpr int kTrainWarps = kTrainThreads / 32;
+constexpr int kTrainRow = kMlpParams + 2;          // gradients, loss sum, valid count
+
+// round-to-nearest-even to bfloat16, back to float
+__device__ __forceinline__ float round_bf16(float f) {
+    uint32_t u = __float_as_uint(f);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    return __uint_as_float(u);
+}
+
+// Gradient of the mean logistic loss over samples start .. start + B - 1
+// (indices taken modulo count; samples with label < 0 skipped).  Layout of
+// the parameters: W1[j][i] at 8 j + i, b1 at 512 + j, W2 at 576 + j, b2 at 640.
+// Each block writes its sums to partial[blockIdx.x][0 .. kTrainRow).
+__global__ void __launch_bounds__(kTrainThreads)
+k_train_grad(const float *x, const float *y, int64_t count, int64_t start, int32_t B,
+             const float *params, float *partial) {
+    __shared__ float W[kMlpParams];
+    __shared__ float acc[kTrainWarps][kTrainRow];
+    for (int q = threadIdx.x; q < kMlpParams; q += kTrainThreads) W[q] = round_bf16(params[q]);
+    for (int q = lane_id(); q < kTrainRow; q += 32) acc[warp_id()][q] = 0.0f;
+    __syncthreads();
+    const int32_t per_round = gridDim.x * kTrainThreads;
+    for (int32_t base = blockIdx.x * kTrainThreads; base < B; base += per_round) {
+        // warp-uniform loop: every lane takes part in the reductions
+        const int32_t t = base + threadIdx.x;
+        bool ok = t < B;
+        float xs[kMlpIn];
+        float yy = 0.0f;
+        if (ok) {
+            int64_t idx = (start + t) % count;
+            yy = y[idx];
+            ok = yy >= 0.0f;
+#pragma unroll
+            for (int i = 0; i < kMlpIn; ++i) xs[i] = x[idx * kMlpIn + i];
+        }
+        if (!ok) {
+#pragma unroll
+            for (int i = 0; i < kMlpIn; ++i) xs[i] = 0.0f;
+        }
+        float a[kMlpHid];
+        float s = W[640];
+#pragma unroll
+        for (int j = 0; j < kMlpHid; ++j) {
+            float h = W[512 + j];
+#pragma unroll
+            for (int i = 0; i < kMlpIn; ++i) h = fmaf(W[j * kMlpIn + i], xs[i], h);
+            a[j] = h;
+            s = fmaf(W[576 + j], h > 0.0f ? h : 0.0f, s);
+        }
+        const float ds = ok ? 1.0f / (1.0f + expf(-s)) - yy : 0.0f;
+        const float loss = ok ? fmaxf(s, 0.0f) - s * yy + log1pf(expf(-fabsf(s))) : 0.0f;
+        float r = warp_sum(loss);
+        float c = warp_sum(ok ? 1.0f : 0.0f);
+        float g2 = warp_sum(ds);
+        if (lane_id() == 0) {
+            acc[warp_id()][kMlpParams] += r;
+            acc[warp_id()][kMlpParams + 1] += c;
+            acc[warp_id()][640] += g2;
+        }
+#pragma unroll
+        for (int j = 0; j < kMlpHid; ++j) {
+            const float h = a[j] > 0.0f ? a[j] : 0.0f;
+            const float da = a[j] > 0.0f ? ds * W[576 + j] : 0.0f;
+            float gw2 = warp_sum(ds * h);
+            float gb1 = warp_sum(da);
+            float gw1[kMlpIn];
+#pragma unroll
+            for (int i = 0; i < kMlpIn; ++i) gw1[i] = warp_sum(da * xs[i]);
+            if (lane_id() == 0) {
+                acc[warp_id()][576 + j] += gw2;
+                acc[warp_id()][512 + j] += gb1;
+#pragma unroll
+                for (int i = 0; i < kMlpIn; ++i) acc[warp_id()][j * kMlpIn + i] += gw1[i];
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTrainRow; q += kTrainThreads) {
+        float v = 0.0f;
+        for (int w = 0; w < kTrainWarps; ++w) v += acc[w][q];
+        partial[(int64_t)blockIdx.x * kTrainRow + q] = v;
+    }
+}
+
+// Sums the blocks' partials in block order and applies one Adam step
+// (Kingma and Ba, 2015) to the float32 master parameters.
+__global__ void k_train_adam(const float *partial, int32_t blocks, float *params, float *m,
+                             float *v, int32_t t, float lr, float beta1, float beta2, float eps,
+                             float *loss_out) {
+    __shared__ float s_cnt;
+    if (threadIdx.x == 0) {
+        float c = 0.0f, l = 0.0f;
+        for (int b = 0; b < blocks; ++b) {
+            c += partial[(int64_t)b * kTrainRow + kMlpParams + 1];
+            l += partial[(int64_t)b * kTrainRow + kMlpParams];
+        }
+        s_cnt = c;
+        if (loss_out) *loss_out = c > 0.0f ? l / c : 0.0f;
+    }
+    __syncthreads();
+    const float cnt = s_cnt;
+    for (int q = threadIdx.x; q < kMlpParams; q += blockDim.x) {
+        float g = 0.0f;
+        for (int b = 0; b < blocks; ++b) g += partial[(int64_t)b * kTrainRow + q];
+        g = cnt > 0.0f ? g / cnt : 0.0f;
+        float mq = beta1 * m[q] + (1.0f - beta1) * g;
+        float vq = beta2 * v[q] + (1.0f - beta2) * g * g;
+        m[q] = mq;
+        v[q] = vq;
+        float mh = mq / (1.0f - powf(beta1, (float)t));
+        float vh = vq / (1.0f - powf(beta2, (float)t));
+        params[q] -= lr * mh / (sqrtf(vh) + eps);
+    }
+}
+
+}  // namespace hgp
+
+using namespace hgp;
+
+extern "C" int hgp_train_mlp(const float *x, const float *y, int64_t count,
+                             const hgp_train_options *opt, float *params, float *adam, float *loss,
+                             void *stream) {
+    if (!x || !y || !opt || !params || !adam || count < 1) return HGP_ERR_INVALID_ARG;
+    if (opt->steps < 0 || opt->batch < 1 || opt->first_step < 1 || !(opt->lr > 0.0f) ||
+        !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
+        !(opt->eps > 0.0f))
+        return HGP_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (opt->reserved[i]) return HGP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int blocks = div_up(opt->batch, kTrainThreads);
+    if (blocks > 128) blocks = 128;
+    float *d_p = nullptr, *d_partial = nullptr, *d_loss = nullptr;
+    size_t np = (size_t)kMlpParams;
+    size_t loss_n = opt->steps > 0 ? (size_t)opt->steps : 1;
+    cudaError_t e = cudaMallocAsync(&d_p, sizeof(float) * 3 * np, s);
+    if (!e) e = cudaMallocAsync(&d_partial, sizeof(float) * (size_t)blocks * kTrainRow, s);
+    if (!e) e = cudaMallocAsync(&d_loss, sizeof(float) * loss_n, s);
+    if (!e) e = cudaMemcpyAsync(d_p, params, sizeof(float) * np, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_p + np, adam, sizeof(float) * 2 * np, cudaMemcpyHostToDevice, s);
+    for (int32_t k = 0; !e && k < opt->steps; ++k) {
+        int64_t start = ((int64_t)k * opt->batch) % count;
+        k_train_grad<<<blocks, kTrainThreads, 0, s>>>(x, y, count, start, opt->batch, d_p, d_partial);
+        k_train_adam<<<1, 704, 0, s>>>(d_partial, blocks, d_p, d_p + np, d_p + 2 * np,
+                                       opt->first_step + k, opt->lr, opt->beta1, opt->beta2, opt->eps,
+                                       d_loss + k);
+        count_launch();
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(params, d_p, sizeof(float) * np, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(adam, d_p + np, sizeof(float) * 2 * np, cudaMemcpyDeviceToHost, s);
+    if (!e && loss && opt->steps > 0)
+        e = cudaMemcpyAsync(loss, d_loss, sizeof(float) * (size_t)opt->steps, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (d_p) cudaFreeAsync(d_p, s);
+    if (d_partial) cudaFreeAsync(d_partial, s);
+    if (d_loss) cudaFreeAsync(d_loss, s);
+    cudaStreamSynchronize(s);
+    return (e || e2) ? HGP_ERR_CUDA : HGP_OK;
+}
+
+extern "C" int hgp_model_from_params(const float *params, int32_t key_bits, hgp_model *out) {
+    if (!params || !out || key_bits < 0 || key_bits > 20) return HGP_ERR_INVALID_ARG;
+    auto to_bf16 = [](float f) -> uint16_t {
+        uint32_t u;
+        memcpy(&u, &f, sizeof(u));
+        return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+    };
+    memset(out, 0, sizeof(*out));
+    for (int q = 0; q < kMlpHid * kMlpIn; ++q) out->w1[q] = to_bf16(params[q]);
+    for (int j = 0; j < kMlpHid; ++j) {
+        out->b1[j] = to_bf16(params[512 + j]);
+        out->w2[j] = to_bf16(params[576 + j]);
+    }
+    out->b2 = to_bf16(params[640]);
+    out->key_bits = (int16_t)key_bits;
+    return HGP_OK;
+}

@@ -66,10 +66,16 @@ static int grid1d(int64_t n) {
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-// pair/score -> match, gamma; *d_V2 receives the coarse node count.
+__global__ void k_best_key(int32_t V, const int32_t *pair, const int32_t *score,
+                           const int32_t *key, unsigned long long *bkey);
+__global__ void k_best_id(int32_t V, const int32_t *pair, const int32_t *score, const int32_t *key,
+                          const unsigned long long *bkey, unsigned long long *best);
+
+// pair/score (and the learned order's keys, or null) -> match, gamma;
+// *d_V2 receives the coarse node count.
 cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
-                      int32_t *match, int32_t *gamma, int32_t *d_V2, int32_t *status,
-                      cudaStream_t s) {
+                      const int32_t *key, int32_t *match, int32_t *gamma, int32_t *d_V2,
+                      int32_t *status, cudaStream_t s) {
     unsigned long long *best = nullptr;
     int32_t *flag = nullptr, *rank = nullptr;
     cudaError_t e = dalloc(ar, &best, V);
@@ -78,8 +84,19 @@ cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *
     if (e) return e;
     e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * (size_t)V, s);
     if (e) return e;
-    k_best<<<grid1d(V), 256, 0, s>>>(V, pair, score, best);
-    count_launch();
+    if (key) {
+        unsigned long long *bkey = nullptr;
+        e = dalloc(ar, &bkey, V);
+        if (!e) e = cudaMemsetAsync(bkey, 0, sizeof(unsigned long long) * (size_t)V, s);
+        if (e) return e;
+        k_best_key<<<grid1d(V), 256, 0, s>>>(V, pair, score, key, bkey);
+        k_best_id<<<grid1d(V), 256, 0, s>>>(V, pair, score, key, bkey, best);
+        count_launch();
+        count_launch();
+    } else {
+        k_best<<<grid1d(V), 256, 0, s>>>(V, pair, score, best);
+        count_launch();
+    }
     k_lock_match<<<grid1d(V), 256, 0, s>>>(V, pair, best, match, flag, status);
     count_launch();
     e = exclusive_scan_i32(ar, flag, rank, V, d_V2, s);

@@ -29,7 +29,8 @@ HGP_DEBUG_FORCE_GLOBAL = 4
 HGP_DEBUG_NO_BITMAP = 8
 HGP_DEBUG_FORCE_CLUSTER = 16
 (HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
- HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE) = range(8)
+ HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE, HGP_LEVEL_KEY) = range(9)
+HGP_MLP_PARAMS = 641
 
 
 class HgpError(RuntimeError):
@@ -38,9 +39,52 @@ class HgpError(RuntimeError):
         self.code = code
 
 
+class hgp_model(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_uint16 * 512), ("b1", ctypes.c_uint16 * 64),
+                ("w2", ctypes.c_uint16 * 64), ("b2", ctypes.c_uint16), ("key_bits", ctypes.c_int16),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
 class hgp_options(ctypes.Structure):
     _fields_ = [("refine_passes", ctypes.c_int32), ("debug", ctypes.c_uint32),
-                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("model", ctypes.POINTER(hgp_model))]
+
+
+class hgp_train_options(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("first_step", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+@dataclass
+class Model:
+    """The learned order's network as bfloat16 bit patterns (see hgp_model)."""
+    w1: np.ndarray      # uint16 [64, 8]
+    b1: np.ndarray      # uint16 [64]
+    w2: np.ndarray      # uint16 [64]
+    b2: int
+    key_bits: int
+
+
+def _c_model(model):
+    if model is None:
+        return None
+    m = hgp_model()
+    ctypes.memmove(m.w1, np.ascontiguousarray(model.w1, dtype=np.uint16).reshape(512).ctypes.data, 1024)
+    ctypes.memmove(m.b1, np.ascontiguousarray(model.b1, dtype=np.uint16).reshape(64).ctypes.data, 128)
+    ctypes.memmove(m.w2, np.ascontiguousarray(model.w2, dtype=np.uint16).reshape(64).ctypes.data, 128)
+    m.b2 = int(model.b2)
+    m.key_bits = int(model.key_bits)
+    return m
+
+
+def _options(refine_passes, debug, max_levels, model):
+    opt = hgp_options(refine_passes, debug, max_levels)
+    cm = _c_model(model)
+    if cm is not None:
+        opt.model = ctypes.pointer(cm)
+    return opt, cm
 
 
 class hgp_result(ctypes.Structure):
@@ -69,7 +113,8 @@ class hgp_stats(ctypes.Structure):
 # every symbol declared in include/hgp.h
 EXPORTS = ("hgp_create", "hgp_partition", "hgp_get_stats", "hgp_get_level_len",
            "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy",
-           "hgp_score_noalloc", "hgp_partition_batch")
+           "hgp_score_noalloc", "hgp_partition_batch", "hgp_learn_samples", "hgp_train_mlp",
+           "hgp_model_from_params")
 
 _lib = None
 
@@ -102,6 +147,12 @@ def load(path: str = LIB_PATH):
     lib.hgp_partition_batch.argtypes = [vp, i32, vp, vp, ctypes.POINTER(hgp_options), vp, vp]
     lib.hgp_partition_batch.restype = ctypes.c_int
     lib.hgp_score_noalloc.restype = ctypes.c_int
+    lib.hgp_learn_samples.argtypes = [vp, vp, ctypes.c_uint64, i32, vp, vp, vp]
+    lib.hgp_learn_samples.restype = ctypes.c_int
+    lib.hgp_train_mlp.argtypes = [vp, vp, i64, ctypes.POINTER(hgp_train_options), vp, vp, vp, vp]
+    lib.hgp_train_mlp.restype = ctypes.c_int
+    lib.hgp_model_from_params.argtypes = [vp, i32, ctypes.POINTER(hgp_model)]
+    lib.hgp_model_from_params.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -159,11 +210,11 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
 
 
 def hgp_partition(handle, omega, delta, part_ids, part_weight=None, part_inbound=None,
-                  refine_passes=1, debug=0, max_levels=0):
+                  refine_passes=1, debug=0, max_levels=0, model=None):
     """hgp_partition into caller buffers (host numpy or device torch tensors).
     Returns (cost, num_parts, num_levels)."""
     lib = load()
-    opt = hgp_options(refine_passes, debug, max_levels)
+    opt, _keep = _options(refine_passes, debug, max_levels, model)
     res = hgp_result()
     res.part_ids = _ptr(part_ids)
     res.part_weight = _ptr(part_weight)
@@ -203,7 +254,7 @@ def hgp_destroy(handle):
         load().hgp_destroy(handle)
 
 
-def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_levels=0):
+def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_levels=0, model=None):
     """Partitions several Graph objects concurrently; returns a list of Result."""
     lib = load()
     n = len(graphs)
@@ -220,7 +271,7 @@ def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_le
         res[i].part_ids, res[i].part_weight, res[i].part_inbound = ids.ctypes.data, pw.ctypes.data, pin.ctypes.data
         res[i].out_flags = 0
     status = np.zeros(max(n, 1), dtype=np.int32)
-    opt = hgp_options(refine_passes, debug, max_levels)
+    opt, _keep = _options(refine_passes, debug, max_levels, model)
     rc = lib.hgp_partition_batch(handles, n, om.ctypes.data, de.ctypes.data, ctypes.byref(opt),
                                  ctypes.addressof(res), status.ctypes.data)
     if rc != HGP_OK:
@@ -231,6 +282,32 @@ def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_le
         k = res[i].num_parts
         out.append(Result(ids, int(res[i].cost), int(k), int(res[i].num_levels), pw[:k], pin[:k]))
     return out
+
+
+def hgp_train_mlp(x, y, params, adam, steps, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  first_step=1, stream=None):
+    """hgp_train_mlp on torch CUDA tensors x [count, 8], y [count]; params
+    (641) and adam (2 x 641) float32 numpy arrays are updated in place.
+    Returns the per-step mean batch losses."""
+    opt = hgp_train_options(int(steps), int(batch), float(lr), float(beta1), float(beta2),
+                            float(eps), int(first_step))
+    if params.dtype != np.float32 or adam.dtype != np.float32 or not params.flags.c_contiguous \
+            or not adam.flags.c_contiguous:
+        raise TypeError("params and adam must be contiguous float32 numpy arrays")
+    loss = np.zeros(max(int(steps), 1), dtype=np.float32)
+    rc = load().hgp_train_mlp(_ptr(x), _ptr(y), int(y.shape[0]), ctypes.byref(opt), _ptr(params),
+                              _ptr(adam), _ptr(loss), _stream_handle(stream))
+    _check(rc, None)
+    return loss[:int(steps)]
+
+
+def hgp_model_from_params(params, key_bits) -> Model:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = hgp_model()
+    _check(load().hgp_model_from_params(_ptr(p), int(key_bits), ctypes.byref(m)), None)
+    return Model(np.frombuffer(bytes(m.w1), dtype=np.uint16).reshape(64, 8).copy(),
+                 np.frombuffer(bytes(m.b1), dtype=np.uint16).copy(),
+                 np.frombuffer(bytes(m.w2), dtype=np.uint16).copy(), int(m.b2), int(m.key_bits))
 
 
 @dataclass
@@ -254,18 +331,33 @@ class Graph:
     def from_hypergraph(cls, g, stream=None):
         return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream)
 
-    def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0) -> Result:
+    def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)
         pw = np.empty(self.num_nodes, dtype=np.int64)
         pin = np.empty(self.num_nodes, dtype=np.int32)
         cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug,
-                                          max_levels)
+                                          max_levels, model)
         return Result(ids, cost, npart, nlev, pw[:npart], pin[:npart])
 
     def partition_device(self, omega, delta, part_ids, part_weight=None, part_inbound=None,
-                         refine_passes=1, debug=0):
+                         refine_passes=1, debug=0, model=None):
         return hgp_partition(self._h, omega, delta, part_ids, part_weight, part_inbound,
-                             refine_passes, debug)
+                             refine_passes, debug, 0, model)
+
+    def learn_samples(self, part_ids, seed, per_node, with_partner=True):
+        """hgp_learn_samples into new torch CUDA tensors: (x [S, 8], y [S],
+        partner [S] or None), S = num_nodes * per_node; part_ids is a torch
+        int32 CUDA tensor."""
+        import torch
+        S = self.num_nodes * int(per_node)
+        dev = part_ids.device
+        x = torch.empty((S, 8), dtype=torch.float32, device=dev)
+        y = torch.empty(S, dtype=torch.float32, device=dev)
+        partner = torch.empty(S, dtype=torch.int32, device=dev) if with_partner else None
+        rc = load().hgp_learn_samples(self._h, _ptr(part_ids), ctypes.c_uint64(int(seed)),
+                                      int(per_node), _ptr(x), _ptr(y), _ptr(partner))
+        _check(rc, self._h)
+        return x, y, partner
 
     def stats(self) -> dict:
         return hgp_get_stats(self._h)
@@ -289,3 +381,34 @@ class Graph:
 
     def __exit__(self, *a):
         self.close()
+
+
+def train_model(graphs, omega, delta, seed=0, per_node=16, steps=2000, batch=4096, lr=3e-3,
+                key_bits=6, init_params=None, stream=None):
+    """The learned order's training pipeline, every step a library call:
+    partition each training graph with the plain order (hgp_partition, part
+    ids kept on the device), draw labelled pairs from it (hgp_learn_samples),
+    train on all of them (hgp_train_mlp) and round the result to a model
+    (hgp_model_from_params).  Returns (model, per-step losses)."""
+    import torch
+    xs, ys = [], []
+    for i, g in enumerate(graphs):
+        with Graph.from_hypergraph(g, stream) as G:
+            ids = torch.empty(g.num_nodes, dtype=torch.int32, device="cuda")
+            G.partition_device(omega, delta, ids)
+            x, y, _ = G.learn_samples(ids, seed * 1_000_003 + i, per_node, with_partner=False)
+            xs.append(x)
+            ys.append(y)
+    x = torch.cat(xs)
+    y = torch.cat(ys)
+    # one fixed shuffle so that consecutive minibatches mix graphs and nodes
+    gen = torch.Generator(device="cpu").manual_seed(int(seed))
+    perm = torch.randperm(x.shape[0], generator=gen).to(x.device)
+    x = x[perm].contiguous()
+    y = y[perm].contiguous()
+    params = (np.zeros(HGP_MLP_PARAMS, np.float32) if init_params is None
+              else np.array(init_params, dtype=np.float32))
+    adam = np.zeros(2 * HGP_MLP_PARAMS, np.float32)
+    torch.cuda.synchronize()
+    losses = hgp_train_mlp(x, y, params, adam, steps, batch, lr, stream=stream)
+    return hgp_model_from_params(params, key_bits), losses
