@@ -274,6 +274,9 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
                                   key_bits=LEARN_KEY_BITS, init_params=synth.initial_params(0),
                                   stream=stream)
     train_s = time.perf_counter() - t0
+    if args.save_model:
+        np.savez(args.save_model, w1=model.w1, b1=model.b1, w2=model.w2, b2=model.b2,
+                 key_bits=model.key_bits)
     step(model=model)
     torch.cuda.synchronize()
     times, stats, res = [], [], None
@@ -317,6 +320,10 @@ def main():
                          "hypergraphs through hgp_partition_batch (prints its own JSON line)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-order leg (training + timed learned partitions)")
+    ap.add_argument("--save-model", default=None,
+                    help="write the learned leg's trained model to this .npz file")
+    ap.add_argument("--learned-model", default=None,
+                    help="with --profile-step: profile one step with this saved model")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run exactly one step, exit (for ncu launch lists)")
     args = ap.parse_args()
@@ -366,7 +373,11 @@ def main():
         step()
     torch.cuda.synchronize()
     if args.profile_step:
-        res, st = step()
+        model = None
+        if args.learned_model:
+            z = np.load(args.learned_model)
+            model = H.Model(z["w1"], z["b1"], z["w2"], int(z["b2"]), int(z["key_bits"]))
+        res, st = step(model=model)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": True, "levels": st["num_levels"], "cost": res[0],
                           "launches": st["kernel_launches"] + st["create_launches"]}))

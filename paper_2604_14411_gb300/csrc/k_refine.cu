@@ -218,7 +218,32 @@ struct PropArgs {
     const int32_t *prev_gain, *prev_pd;   // proposals of the coarser level (null = none)
     const int32_t *gamma, *match;         // this level's map to the coarser level
     const int32_t *prev_applied;          // device flag: the coarser pass applied moves
+    const int32_t *list;                  // nodes left to compute (the others were reused)
+    int32_t *count;
 };
+
+// Reused proposals are copied here, one thread per node; every other node is
+// appended to the work list of k_propose, so reuse costs the CTAs nothing.
+__global__ void k_prop_worklist(PropArgs a) {
+    const bool reuse = a.prev_gain && *a.prev_applied == 0;
+    unsigned long long nbytes = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.V;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = (int32_t)i;
+        if (reuse && a.match[n] == n) {
+            int32_t c = a.gamma[n];
+            a.gain[n] = a.prev_gain[c];
+            a.pd[n] = a.prev_pd[c];
+            nbytes += 24ull;
+        } else {
+            const_cast<int32_t *>(a.list)[atomicAdd(a.count, 1)] = n;
+        }
+    }
+    if (a.bytes) {
+        nbytes = warp_sum(nbytes);
+        if (lane_id() == 0 && nbytes) atomicAdd(a.bytes, nbytes);
+    }
+}
 
 template <bool DENSE>
 __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
@@ -233,20 +258,15 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
     unsigned long long nbytes = 0;
     for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
     if (threadIdx.x == 0) s_nt = 0;
+    const int32_t work = *a.count;
     for (;;) {
-        if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
+        if (threadIdx.x == 0) {
+            int32_t t = atomicAdd(a.next, 1);
+            s_n = t < work ? a.list[t] : a.V;
+        }
         __syncthreads();
         const int32_t n = s_n;
         if (n >= a.V) break;
-        if (a.prev_gain && *a.prev_applied == 0 && a.match[n] == n) {
-            if (threadIdx.x == 0) {
-                int32_t c = a.gamma[n];
-                a.gain[n] = a.prev_gain[c];
-                a.pd[n] = a.prev_pd[c];
-            }
-            __syncthreads();
-            continue;
-        }
         int32_t ps = a.rho[n];
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
         long long sav = 0, wI = 0;
@@ -756,9 +776,14 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     pa.nrun = R.nrun; pa.omega = omega; pa.gain = pg; pa.pd = ppd;
     pa.prev_gain = ru.prev_gain; pa.prev_pd = ru.prev_pd;
     pa.gamma = ru.gamma; pa.match = ru.match; pa.prev_applied = ru.applied_flag;
-    e = dalloc(tmp, &pa.next, 1);
-    if (!e) e = cudaMemsetAsync(pa.next, 0, sizeof(int32_t), s);
+    int32_t *wl = nullptr, *wcount = nullptr;
+    e = dalloc(tmp, &pa.next, 2);
+    if (!e) e = dalloc(tmp, &wl, V);
+    if (!e) e = cudaMemsetAsync(pa.next, 0, 2 * sizeof(int32_t), s);
     if (e) return e;
+    wcount = pa.next + 1;
+    pa.list = wl;
+    pa.count = wcount;
     pa.bytes = pt ? pt->bytes : nullptr;
     if (pt) {
         cudaEvent_t ev;
@@ -766,6 +791,8 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         cudaEventRecord(ev, s);
         pt->ev.push_back({ev, nullptr});
     }
+    k_prop_worklist<<<grid1d(V), 256, 0, s>>>(pa);
+    count_launch();
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
         size_t smem = 2 * sizeof(int32_t) * (size_t)K;
