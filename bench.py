@@ -41,6 +41,7 @@ OMEGA, DELTA = 1 << 10, 1 << 12
 WORKLOAD = "random SNN hypergraph, 16,384 nodes, one hyperedge per node of 128 pins (src + 127 distinct targets), 2,097,152 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0"
 LEARN_TRAIN_GRAPHS, LEARN_PER_NODE, LEARN_STEPS, LEARN_BATCH, LEARN_LR, LEARN_KEY_BITS = \
     4, 16, 2000, 4096, 3e-3, 6
+LEARN_SM_GHZ = 2.07          # maximum SM clock of the GB300
 SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same generator family "
                "(32 pins per hyperedge, 65,536 pins, Omega=128, Delta=512, seed 0); the 16k-node "
                "workload needs well over 10 minutes of oracle time on one core")
@@ -227,6 +228,30 @@ def run_batch(args, rank, world):
     for G in graphs:
         G.partition(OMEGA, DELTA)
     seq_ms = 1000.0 * (time.perf_counter() - t0)
+    learned = None
+    if not args.no_learned:
+        # the same batch with the learned order (model trained untimed on 16k-node graphs)
+        t0 = time.perf_counter()
+        model, _ = H.train_model(synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,)),
+                                 OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE, steps=LEARN_STEPS,
+                                 batch=LEARN_BATCH, lr=LEARN_LR, key_bits=LEARN_KEY_BITS,
+                                 init_params=synth.initial_params(0))
+        train_s = time.perf_counter() - t0
+        H.hgp_partition_batch(graphs, om, de, model=model)
+        torch.cuda.synchronize()
+        lt = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            lres = H.hgp_partition_batch(graphs, om, de, model=model)
+            torch.cuda.synchronize()
+            lt.append(1000.0 * (time.perf_counter() - t0))
+        lms = statistics.median(lt)
+        feas = all(recount(g, r.part_ids, OMEGA, DELTA)[1] for g, r in zip(inst, lres))
+        lcost = int(sum(r.cost for r in lres))
+        learned = {"ms_per_step": lms, "pins_per_s": pins / (lms / 1000.0), "total_cost": lcost,
+                   "cost_ratio_vs_plain": lcost / max(1, int(sum(r.cost for r in res))),
+                   "time_ratio_vs_plain": lms / (job / args.steps), "all_feasible": feas,
+                   "training_seconds": train_s, "steps": len(lt)}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": job_value(pins, args.steps, world, job), "unit": "pins/s",
@@ -237,7 +262,7 @@ def run_batch(args, rank, world):
                        "timing": "host clock around hgp_partition_batch (device-resident inputs)"},
             "sequential_ms": seq_ms, "batch_speedup_vs_sequential": seq_ms / (job / args.steps),
             "total_cost": int(sum(r.cost for r in res)), "total_parts": int(sum(r.num_parts for r in res)),
-            "clocks": clocks}), flush=True)
+            "clocks": clocks, **({"learned": learned} if learned else {})}), flush=True)
     for G in graphs:
         G.close()
     if dist:
@@ -293,6 +318,13 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
     ms = statistics.median(times)
     ids = d_ids.cpu().numpy()
     cost, feasible = recount(g, ids, OMEGA, DELTA)
+    # the learned scorer's FP32 roofline: 1,152 FLOP per network evaluation
+    # (64 x 8 + 64 FMA) against 152 SMs x 128 FP32 lanes x 2 FLOP x the SM clock
+    sc_ms = sum(s["ms_score"] for s in stats)
+    evals = sum(s["learned_evals"] for s in stats)
+    flops = 1152.0 * evals
+    peak_tflops = 152 * 128 * 2 * LEARN_SM_GHZ / 1000.0
+    achieved = flops / (sc_ms / 1000.0) / 1e12 if sc_ms > 0 else 0.0
     return {"model": f"8-64-1 MLP, bfloat16 weights, key_bits {LEARN_KEY_BITS}",
             "training": {"graphs": f"{LEARN_TRAIN_GRAPHS} random SNN hypergraphs, 16,384 nodes, "
                                    "hyperedge size 128..256, seeds 100..", "labels": "co-location in "
@@ -305,7 +337,104 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
             "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
             "cost_recounted": cost, "feasible": feasible,
             "cost_ratio_vs_plain": res[0] / plain_cost, "time_ratio_vs_plain": ms / plain_ms,
-            "steps": len(times)}
+            "steps": len(times),
+            "roofline": {"kernel": "k_score_learned (network-ranked scoring)", "bound": "alu",
+                         "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": None,
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                         "evals_per_step": evals / len(stats),
+                         "score_ms_per_step": sc_ms / len(stats),
+                         "hbm_achieved_gbs": (sum(s["score_bytes"] for s in stats) / 1e9) / (sc_ms / 1000.0)
+                         if sc_ms > 0 else 0.0}}
+
+
+LEARNED256K_WORKLOAD = ("learned candidate order on a random SNN hypergraph, 262,144 nodes, one "
+                        "hyperedge per node of 256 pins, 67,108,864 pins, int32 CSR, Omega=2^10, "
+                        "Delta=2^12, seed 0; model trained on 4 seeded 16,384-node graphs")
+
+
+def run_learned256k(args, rank, world):
+    """The learned order on the 262,144-node SNN: train (untimed), then time
+    whole partitions (create + partition + destroy, device-resident inputs)."""
+    import torch
+    import synth
+    from paper_2604_14411_gb300 import hgp as H
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    H.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    model, losses = H.train_model(synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,)),
+                                  OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE, steps=LEARN_STEPS,
+                                  batch=LEARN_BATCH, lr=LEARN_LR, key_bits=LEARN_KEY_BITS,
+                                  init_params=synth.initial_params(0), stream=stream)
+    train_s = time.perf_counter() - t0
+    g = synth.snn_256k(0)
+    N, P = g.num_nodes, g.num_pins
+    d_off = torch.from_numpy(g.offsets.copy()).to(dev)
+    d_pins = torch.from_numpy(g.pins.copy()).to(dev)
+    d_ids = torch.empty(N, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(debug=0):
+        h = H.hgp_create(N, d_off, d_pins, stream=stream)
+        try:
+            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, None, None, 1, debug, 0, model)
+            st = H.hgp_get_stats(h)
+        finally:
+            H.hgp_destroy(h)
+        return res, st
+
+    warm = 1 if args.warmup >= 1 else 0
+    for _ in range(warm):
+        step()
+    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    times, stats, res = [], [], None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, st = step(H.HGP_DEBUG_TIMING)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        stats.append(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop(local)
+    job = job_time_ms(sum(times), dist, dev)
+    ids = d_ids.cpu().numpy()
+    cost, feasible = recount(g, ids, OMEGA, DELTA)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_value(P, args.steps, world, job), "unit": "pins/s",
+            "n_gpus": world, "steps": args.steps, "warmup": warm, "ms_per_step": job / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": LEARNED256K_WORKLOAD, "omega": OMEGA, "delta": DELTA, "pins": P,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
+            "coarsening_pins_per_s": P / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
+            "refine_ms": statistics.median(s["ms_refine"] for s in stats),
+            "score_ms": statistics.median(s["ms_score"] for s in stats),
+            "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
+            "cost_recounted": cost, "feasible": feasible,
+            "training_seconds": train_s, "loss_last": float(losses[-20:].mean()),
+            "gpu_launches": int(stats[-1]["kernel_launches"] + stats[-1]["create_launches"]) * args.steps,
+            "clocks": clocks}), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def main():
@@ -315,9 +444,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="snn16k", choices=["snn16k", "batch64"],
+    ap.add_argument("--workload", default="snn16k", choices=["snn16k", "batch64", "learned256k"],
                     help="snn16k: the default single-hypergraph workload; batch64: 64 uneven "
-                         "hypergraphs through hgp_partition_batch (prints its own JSON line)")
+                         "hypergraphs through hgp_partition_batch; learned256k: the learned order "
+                         "on the 262,144-node SNN (the last two print their own JSON line)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-order leg (training + timed learned partitions)")
     ap.add_argument("--save-model", default=None,
@@ -337,6 +467,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch64":
         return run_batch(args, rank, world)
+    if args.workload == "learned256k":
+        return run_learned256k(args, rank, world)
 
     import torch
     import synth

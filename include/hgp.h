@@ -202,6 +202,8 @@ typedef struct {
     double ms_propose;         /* HGP_DEBUG_TIMING: Eq. (3) proposal kernel, summed */
     int64_t propose_launches;
     int64_t propose_bytes;     /* algorithmic bytes of all proposal launches */
+    int64_t learned_evals;     /* HGP_DEBUG_TIMING, learned order: network evaluations (each
+                                  8 lg1p features + 576 FMA + 64 ReLU) over all levels */
 } hgp_stats;
 
 /* Statistics of the handle's last hgp_partition (and hgp_create). */

@@ -17,7 +17,8 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
 cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
                               int64_t delta, const hgp_model *model, int32_t *pair,
                               int32_t *score, int32_t *key, int32_t *status,
-                              unsigned long long *bytes, uint32_t debug, cudaStream_t s);
+                              unsigned long long *bytes, unsigned long long *evals,
+                              uint32_t debug, cudaStream_t s);
 bool model_valid(const hgp_model *m);
 cudaError_t run_learn_samples(const Level &L0, const int32_t *ew, const int32_t *part_ids,
                               uint64_t seed, int32_t per_node, float *x, float *y,
@@ -317,9 +318,9 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     unsigned long long *d_bytes = nullptr;
     CKP(dalloc(lv, &d_status, 1), "alloc");
     CKP(dalloc(lv, &d_V2, 1), "alloc");
-    CKP(dalloc(lv, &d_bytes, 1), "alloc");
+    CKP(dalloc(lv, &d_bytes, 2), "alloc");          // [0] scoring bytes, [1] network evaluations
     CKP(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s), "memset");
-    CKP(cudaMemsetAsync(d_bytes, 0, sizeof(unsigned long long), s), "memset");
+    CKP(cudaMemsetAsync(d_bytes, 0, 2 * sizeof(unsigned long long), s), "memset");
 
     int64_t target = g->W / omega + (g->W % omega != 0);
     std::vector<Level> levels;
@@ -346,7 +347,8 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
             tm.start(0, &ev_a);
             if (model)
                 CKP(run_score_learned(tmp, L, g->ew, omega, delta, model, pair, score, key, d_status,
-                                      tm.on ? d_bytes : nullptr, debug, s), "score");
+                                      tm.on ? d_bytes : nullptr, tm.on ? d_bytes + 1 : nullptr,
+                                      debug, s), "score");
             else
                 CKP(run_score(tmp, L, g->ew, omega, delta, pair, score, d_status,
                               tm.on ? d_bytes : nullptr, debug, s), "score");
@@ -512,6 +514,9 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         unsigned long long b = 0;
         cudaMemcpy(&b, d_bytes, sizeof(b), cudaMemcpyDeviceToHost);
         st.score_bytes = (int64_t)b;
+        unsigned long long ev = 0;
+        cudaMemcpy(&ev, d_bytes + 1, sizeof(ev), cudaMemcpyDeviceToHost);
+        st.learned_evals = (int64_t)ev;
         double tp = 0;
         for (auto &pr : ptime.ev) {
             float ms = 0;

@@ -57,9 +57,9 @@ struct LearnedArgs {
     int64_t omega, delta;
     int32_t *pair, *score, *key;
     int32_t *next, *status;
-    int32_t *gkeys, *gvals, *ginter;
+    int32_t *gkeys, *gvals, *ginter, *gused;
     int32_t gcap;
-    unsigned long long *bytes;
+    unsigned long long *bytes, *evals;
 };
 
 __device__ __forceinline__ float pow2_exact(int k) {       // 2^k, -126 <= k <= 127
@@ -142,13 +142,19 @@ k_score_learned(LearnedArgs a, MlpParams M) {
     int32_t *inter = hist + (DENSE ? a.V : 0);
     __shared__ unsigned long long s_c[kLearnWarps];
     __shared__ int32_t s_i[kLearnWarps];
-    __shared__ int32_t s_n;
+    __shared__ int32_t s_n, s_used;
+    // hash mode: the table is cleared once here, then only the slots a node
+    // used (listed in gu) are visited and reset
     int32_t *gk = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
     int32_t *gv = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
     int32_t *gi = DENSE ? nullptr : a.ginter + (int64_t)blockIdx.x * a.gcap;
-    const int32_t cap = DENSE ? a.V : a.gcap;
+    int32_t *gu = DENSE ? nullptr : a.gused + (int64_t)blockIdx.x * a.gcap;
     const uint32_t mask = (uint32_t)a.gcap - 1u;
-    unsigned long long bytes = 0;
+    unsigned long long bytes = 0, evals = 0;
+    if (!DENSE) {
+        for (int32_t i = threadIdx.x; i < a.gcap; i += kLearnThreads) { gk[i] = -1; gv[i] = 0; gi[i] = 0; }
+        if (threadIdx.x == 0) s_used = 0;
+    }
 
     for (;;) {
         if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
@@ -160,10 +166,8 @@ k_score_learned(LearnedArgs a, MlpParams M) {
             __syncthreads();
             continue;
         }
-        for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
-            if (DENSE) { hist[i] = 0; inter[i] = 0; }
-            else { gk[i] = -1; gv[i] = 0; gi[i] = 0; }
-        }
+        if (DENSE)
+            for (int32_t i = threadIdx.x; i < a.V; i += kLearnThreads) { hist[i] = 0; inter[i] = 0; }
         __syncthreads();
         // ---- pass 1: hist(n, .) and inter(n, .) ----
         const int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
@@ -197,6 +201,7 @@ k_score_learned(LearnedArgs a, MlpParams M) {
                         uint32_t slot = hash_node((uint32_t)m) & mask;
                         for (int32_t probes = 0;; ++probes) {
                             int32_t kk = atomicCAS(&gk[slot], -1, m);
+                            if (kk == -1) gu[atomicAdd(&s_used, 1)] = (int32_t)slot;
                             if (kk == -1 || kk == m) {
                                 atomicAdd(&gv[slot], wt);
                                 if (both) atomicAdd(&gi[slot], 1);
@@ -216,10 +221,11 @@ k_score_learned(LearnedArgs a, MlpParams M) {
         const int64_t wn = a.w[n];
         unsigned long long best_c = 0ull;
         int32_t best_m = -1;
+        const int32_t cap = DENSE ? a.V : s_used;
         for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
             int32_t m, h, it;
             if (DENSE) { m = i; h = hist[i]; it = inter[i]; }
-            else { m = gk[i]; h = m >= 0 ? gv[i] : 0; it = m >= 0 ? gi[i] : 0; }
+            else { int32_t sl = gu[i]; m = gk[sl]; h = gv[sl]; it = gi[sl]; }
             if (h == 0) continue;
             if (a.dead && a.dead[m]) continue;
             if (wn + a.w[m] > a.omega) continue;
@@ -232,6 +238,7 @@ k_score_learned(LearnedArgs a, MlpParams M) {
             const unsigned long long c = composite(k, h);
             if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
             bytes += 20ull;
+            evals += 1ull;
         }
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) {
@@ -240,11 +247,21 @@ k_score_learned(LearnedArgs a, MlpParams M) {
             a.key[n] = best_m >= 0 ? (int32_t)(best_c >> 32) - kKeyBias : 0;
             bytes += 24ull;
         }
+        if (!DENSE) {
+            for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
+                int32_t sl = gu[i];
+                gk[sl] = -1; gv[sl] = 0; gi[sl] = 0;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_used = 0;
+        }
         __syncthreads();
     }
     if (a.bytes) {
         bytes = warp_sum(bytes);
+        evals = warp_sum(evals);
         if (lane_id() == 0 && bytes) atomicAdd(a.bytes, bytes);
+        if (lane_id() == 0 && evals && a.evals) atomicAdd(a.evals, evals);
     }
 }
 
@@ -293,7 +310,8 @@ static MlpParams widen(const hgp_model *m) {
 cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
                               int64_t delta, const hgp_model *model, int32_t *pair,
                               int32_t *score, int32_t *key, int32_t *status,
-                              unsigned long long *bytes, uint32_t debug, cudaStream_t s) {
+                              unsigned long long *bytes, unsigned long long *evals,
+                              uint32_t debug, cudaStream_t s) {
     if (L.V <= 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -305,6 +323,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     a.noff = L.noff; a.ew = ew; a.src = L.src; a.sdst = L.sdst; a.dead = L.dead;
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score; a.key = key; a.status = status; a.bytes = bytes;
+    a.evals = evals;
     const MlpParams M = widen(model);
     cudaError_t e = dalloc(ar, &a.next, 1);
     if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
@@ -345,6 +364,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     e = dalloc(ar, &a.gkeys, (size_t)blocks * gcap);
     if (!e) e = dalloc(ar, &a.gvals, (size_t)blocks * gcap);
     if (!e) e = dalloc(ar, &a.ginter, (size_t)blocks * gcap);
+    if (!e) e = dalloc(ar, &a.gused, (size_t)blocks * gcap);
     if (e) return e;
     k_score_learned<false><<<blocks, kLearnThreads, 0, s>>>(a, M);
     count_launch();

@@ -104,7 +104,8 @@ class hgp_stats(ctypes.Structure):
                 ("contract_bytes", ctypes.c_int64), ("pins_total", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("moves_applied", ctypes.c_int64),
                 ("create_launches", ctypes.c_int64), ("ms_propose", ctypes.c_double),
-                ("propose_launches", ctypes.c_int64), ("propose_bytes", ctypes.c_int64)]
+                ("propose_launches", ctypes.c_int64), ("propose_bytes", ctypes.c_int64),
+                ("learned_evals", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

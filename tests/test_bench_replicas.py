@@ -56,3 +56,17 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_recount_matches_the_oracle():
+    """bench.py's host-side recount of cost and feasibility (used for the
+    learned order's results) against the oracle's own partition."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synth
+    g = synth.random_snn(700, 14, 2, size_max=30)
+    r = oracle.partition(g, 24, 160)
+    assert bench.recount(g, r.part_ids, 24, 160) == (r.cost, True)
+    assert bench.recount(g, r.part_ids, int(r.part_weight.max()) - 1, 160)[1] is False
+    assert bench.recount(g, r.part_ids, 24, int(r.part_inbound.max()) - 1)[1] is False

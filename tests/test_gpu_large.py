@@ -90,3 +90,32 @@ def test_first_level_full_size(name, make, omega, delta):
     assert np.array_equal(inbound[:res.num_parts], res.part_inbound)
     assert weight.max() <= omega and inbound.max() <= delta
     assert res.num_parts == g.num_nodes - int((match != np.arange(g.num_nodes)).sum()) // 2
+
+
+def test_learned_order_on_the_256k_snn():
+    """The learned candidate order at full size (262,144 nodes, 67M pins): the
+    first level in the scorer's hash-table mode with a seeded random model,
+    48 sampled nodes' candidate, score and key against the oracle; then a
+    whole partition with a model trained on the GPU, recounted."""
+    g = synth.snn_256k(0)
+    model_r = synth.random_model(13, 0.3, 6)
+    with hgp.Graph.from_hypergraph(g) as G:
+        G.partition(1 << 10, 1 << 12, refine_passes=0, max_levels=1,
+                    debug=H.HGP_DEBUG_KEEP_LEVELS, model=model_r)
+        pair, score, key = (G.level_array(0, w) for w in (H.HGP_LEVEL_PAIR, H.HGP_LEVEL_SCORE,
+                                                           H.HGP_LEVEL_KEY))
+        match = G.level_array(0, H.HGP_LEVEL_MATCH)
+        model, _ = H.train_model(synth.training_graphs(2, 100), 1 << 10, 1 << 12, seed=0,
+                                 per_node=16, steps=1000, batch=4096, key_bits=6)
+        res = G.partition(1 << 10, 1 << 12, model=model)
+    check_matching(pair, match)
+    nodes = np.random.default_rng(99).choice(g.num_nodes, size=48, replace=False).astype(np.int32)
+    with oracle.Run.from_graph(g) as r:
+        p, s, k = r.score0_learned_nodes(1 << 10, 1 << 12, model_r, nodes)
+    assert np.array_equal(pair[nodes], p) and np.array_equal(score[nodes], s)
+    assert np.array_equal(key[nodes], k)
+    cost, weight, inbound = recount(g, res.part_ids)
+    assert cost == res.cost
+    assert weight.max() <= 1 << 10 and inbound.max() <= 1 << 12
+    assert np.array_equal(weight[:res.num_parts], res.part_weight)
+    assert np.array_equal(inbound[:res.num_parts], res.part_inbound)
