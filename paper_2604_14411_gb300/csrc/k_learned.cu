@@ -25,10 +25,19 @@
 // level fits on chip, otherwise per-CTA open-addressing tables in global
 // memory.
 //
+// Levels too large for one CTA but with weighted degrees and inbound counts
+// below 2^16 use a thread-block cluster of 8 CTAs instead: each holds a slice
+// of node ids with hist and inter packed into one 32-bit word (hist << 16 |
+// inter) in its shared memory, the cluster's warps add into the owners'
+// slices with remote shared-memory atomics, each CTA evaluates the network
+// on its own slice, and the cluster reduces (key, hist, id).  Other levels
+// fall back to per-CTA hash tables in global memory.
+//
 // Training kernels: features and co-location labels of sampled pairs, and
 // minibatch Adam steps on the logistic loss with the forward pass in
 // bfloat16 weights and float32 arithmetic; per-warp partial gradients are
 // summed in a fixed order, so training is deterministic.
+#include <cooperative_groups.h>
 #include <cstring>
 
 #include "hgp_internal.cuh"
@@ -265,18 +274,139 @@ k_score_learned(LearnedArgs a, MlpParams M) {
     }
 }
 
+namespace cg = cooperative_groups;
+constexpr int kLearnCluster = 8;
+
+__global__ void __cluster_dims__(kLearnCluster, 1, 1) __launch_bounds__(kLearnThreads)
+k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);      // [slice]: hist << 16 | inter
+    __shared__ unsigned long long s_c[kLearnWarps];
+    __shared__ int32_t s_i[kLearnWarps];
+    __shared__ int32_t s_node;
+    __shared__ unsigned long long s_xc;
+    __shared__ int32_t s_xi;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int32_t id0 = rank * slice;
+    const int32_t len = max(0, min(slice, a.V - id0));
+    unsigned long long bytes = 0, evals = 0;
+    for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) cnt[i] = 0u;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            int32_t t = atomicAdd(a.next, 1);
+            s_node = t < a.V ? t : a.V;
+        }
+        cl.sync();                                   // slices cleared, node published
+        const int32_t n = *cl.map_shared_rank(&s_node, 0);
+        if (n >= a.V) {
+            cl.sync();       // no CTA leaves while a peer may still read its shared memory
+            break;
+        }
+        if (a.dead && a.dead[n]) {
+            if (rank == 0 && threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; a.key[n] = 0; }
+            cl.sync();                               // everyone has read s_node
+            continue;
+        }
+        // ---- pass 1: packed hist / inter over the cluster's warps ----
+        const int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
+        const int32_t gw = rank * kLearnWarps + warp_id(), nw = kLearnCluster * kLearnWarps;
+        const int32_t mine = (i1 - i0 - gw + nw - 1) / nw;
+        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
+            int32_t we = 0, p0 = 0, p1 = 0, se = -1, sd = 0;
+            if (r0 + lane_id() < mine) {
+                int32_t e = a.inc[i0 + gw + nw * (r0 + lane_id())];
+                we = a.ew[e];
+                p0 = a.poff[e];
+                p1 = a.poff[e + 1];
+                se = a.src[e];
+                sd = a.sdst[e];
+            }
+            const int32_t c = min(32, mine - r0);
+            for (int32_t t = 0; t < c; ++t) {
+                const uint32_t wt = (uint32_t)__shfl_sync(0xffffffffu, we, t);
+                const int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
+                const int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
+                const int32_t s_e = __shfl_sync(0xffffffffu, se, t);
+                const int32_t sd_e = __shfl_sync(0xffffffffu, sd, t);
+                const bool n_in = s_e != n || sd_e;
+                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
+                    const int32_t m = a.pins[j];
+                    if (m == n) continue;
+                    const uint32_t both = (n_in && (m != s_e || sd_e)) ? 1u : 0u;
+                    const int32_t owner = m / slice;
+                    atomicAdd(cl.map_shared_rank(cnt, owner) + (m - owner * slice), (wt << 16) | both);
+                }
+                if (lane_id() == 0) bytes += 24ull + 4ull * (unsigned long long)(b1 - b0);
+            }
+        }
+        cl.sync();                                   // every slice complete
+        // ---- pass 2: the network on this CTA's slice ----
+        const int64_t in_n = a.noff[n + 1] - a.noff[n];
+        const int64_t wn = a.w[n];
+        unsigned long long best_c = 0ull;
+        int32_t best_m = -1;
+        for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) {
+            const uint32_t v = cnt[i];
+            const int32_t h = (int32_t)(v >> 16), it = (int32_t)(v & 0xffffu), m = id0 + i;
+            if (h == 0) continue;
+            if (a.dead && a.dead[m]) continue;
+            if (wn + a.w[m] > a.omega) continue;
+            const int64_t in_m = a.noff[m + 1] - a.noff[m];
+            const int64_t uni = in_n + in_m - it;
+            if (uni > a.delta) continue;
+            float x[kMlpIn];
+            features(a, n, m, h, uni, in_n, in_m, x);
+            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
+            const unsigned long long cc = composite(k, h);
+            if (best_m < 0 || cc > best_c || (cc == best_c && m > best_m)) { best_c = cc; best_m = m; }
+            bytes += 20ull;
+            evals += 1ull;
+        }
+        block_argmax(best_c, best_m, s_c, s_i);
+        if (threadIdx.x == 0) { s_xc = best_c; s_xi = best_m; }
+        for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) cnt[i] = 0u;
+        cl.sync();                                   // every CTA's best published
+        if (rank == 0 && threadIdx.x == 0) {
+            unsigned long long bc = 0ull;
+            int32_t bm = -1;
+            for (int r = 0; r < kLearnCluster; ++r) {
+                unsigned long long c2 = *cl.map_shared_rank(&s_xc, r);
+                int32_t m2 = *cl.map_shared_rank(&s_xi, r);
+                if (m2 >= 0 && (bm < 0 || c2 > bc || (c2 == bc && m2 > bm))) { bc = c2; bm = m2; }
+            }
+            a.pair[n] = bm;
+            a.score[n] = bm >= 0 ? (int32_t)(bc & 0xffffffffull) : 0;
+            a.key[n] = bm >= 0 ? (int32_t)(bc >> 32) - kKeyBias : 0;
+            bytes += 24ull;
+        }
+        cl.sync();                                   // rank 0 has read every s_xc / s_xi
+    }
+    if (a.bytes) {
+        bytes = warp_sum(bytes);
+        evals = warp_sum(evals);
+        if (lane_id() == 0 && bytes) atomicAdd(a.bytes, bytes);
+        if (lane_id() == 0 && evals && a.evals) atomicAdd(a.evals, evals);
+    }
+}
+
+// out[0] = largest sum of |e| over I(n) (pin visits of a node); out[1] =
+// largest sum of omega(e) over I(n) (bounds every hist(n, .)).
 static __global__ void k_max_visits(int32_t V, const int32_t *ioff, const int32_t *inc,
-                                    const int32_t *poff, unsigned long long *out) {
+                                    const int32_t *poff, const int32_t *ew,
+                                    unsigned long long *out) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t n = gw; n < V; n += nw) {
-        unsigned long long s = 0;
+        unsigned long long s = 0, w = 0;
         for (int32_t k = ioff[n] + lane_id(); k < ioff[n + 1]; k += 32) {
             int32_t e = inc[k];
             s += (unsigned long long)(poff[e + 1] - poff[e]);
+            w += (unsigned long long)ew[e];
         }
         s = warp_sum(s);
-        if (lane_id() == 0) atomicMax(out, s);
+        w = warp_sum(w);
+        if (lane_id() == 0) { atomicMax(&out[0], s); atomicMax(&out[1], w); }
     }
 }
 
@@ -345,15 +475,49 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
         return cudaGetLastError();
     }
     unsigned long long *d_work = nullptr;
-    e = dalloc(ar, &d_work, 1);
-    if (!e) e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), s);
+    e = dalloc(ar, &d_work, 2);
+    if (!e) e = cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned long long), s);
     if (e) return e;
-    k_max_visits<<<sms * 8, 256, 0, s>>>(L.V, L.ioff, L.inc, L.poff, d_work);
+    k_max_visits<<<sms * 8, 256, 0, s>>>(L.V, L.ioff, L.inc, L.poff, ew, d_work);
     count_launch();
-    unsigned long long h_work = 0;
-    e = cudaMemcpyAsync(&h_work, d_work, sizeof(h_work), cudaMemcpyDeviceToHost, s);
+    unsigned long long h_max[2] = {0, 0};
+    e = cudaMemcpyAsync(h_max, d_work, sizeof(h_max), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return e;
+    const unsigned long long h_work = h_max[0];
+    // packed 16-bit counters fit: every hist(n, .) <= sum of omega over I(n),
+    // every inter(n, .) <= |in(n)|
+    const int32_t slice = (L.V + kLearnCluster - 1) / kLearnCluster;
+    const size_t cl_smem = sizeof(uint32_t) * (size_t)slice;
+    if (!(debug & HGP_DEBUG_FORCE_GLOBAL) && h_max[1] < 65536ull && L.max_in < 65536 &&
+        cl_smem + 4096 <= (size_t)max_smem) {
+        e = allow_dynamic_smem(k_score_learned_cluster);
+        if (e) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(kLearnThreads);
+        cfg.dynamicSmemBytes = cl_smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = kLearnCluster;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(kLearnCluster);
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_score_learned_cluster, &cfg) != cudaSuccess ||
+            clusters < 1)
+            clusters = 1;
+        (void)cudaGetLastError();
+        if (clusters > L.V) clusters = L.V;
+        cfg.gridDim = dim3(kLearnCluster * clusters);
+        cfg.attrs = nullptr;       // the cluster shape comes from __cluster_dims__
+        cfg.numAttrs = 0;
+        e = cudaLaunchKernelEx(&cfg, k_score_learned_cluster, a, M, slice);
+        count_launch();
+        return e ? e : cudaGetLastError();
+    }
     unsigned long long distinct = h_work < (unsigned long long)L.V ? h_work : (unsigned long long)L.V;
     unsigned long long gcap = 64;
     while (gcap < 2 * distinct) gcap <<= 1;

@@ -61,3 +61,45 @@ def test_error_strings_without_gpu():
     # invalid arguments are rejected on the host before any device work
     h = ctypes.c_void_p()
     assert lib.hgp_create(0, 0, None, None, None, None, 0, None, ctypes.byref(h)) == 1
+
+
+def test_struct_layouts_match_the_header():
+    """The binding's ctypes structs have the sizes the header implies."""
+    from paper_2604_14411_gb300 import hgp as H
+    assert ctypes.sizeof(H.hgp_model) == 2 * (512 + 64 + 64 + 1) + 2 + 12
+    assert ctypes.sizeof(H.hgp_options) == 32
+    assert H.hgp_options.model.offset == 24
+    assert ctypes.sizeof(H.hgp_train_options) == 40
+
+
+def test_model_from_params_rounds_to_nearest_even():
+    """hgp_model_from_params is host-only; its bfloat16 rounding against the
+    exact value: the nearest bfloat16, ties to an even mantissa."""
+    from paper_2604_14411_gb300 import _build
+    from paper_2604_14411_gb300 import hgp as H
+    _build.build()
+    try:
+        H.load()
+    except OSError as e:
+        pytest.skip(f"cannot dlopen without the CUDA driver: {e}")
+    import numpy as np
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=641).astype(np.float32)
+    # exact ties: bit 15 set and nothing below it
+    p[:4] = (np.array([0x3F808000, 0x3F818000, 0xBF808000, 0x40000000], np.uint32)).view(np.float32)
+    m = H.hgp_model_from_params(p, 7)
+    got = np.concatenate([m.w1.reshape(-1), m.b1, m.w2, [m.b2]]).astype(np.uint32)
+    exact = p.astype(np.float64)
+    lo = (p.view(np.uint32) >> 16).astype(np.uint32)
+    for q in range(641):
+        cands = [int(lo[q]), int(lo[q]) + 1]
+        vals = [(np.uint32(c) << 16).view(np.float32).astype(np.float64) for c in cands]
+        d = [abs(v - exact[q]) for v in vals]
+        if d[0] != d[1]:
+            assert got[q] == cands[int(d[1] < d[0])], q
+        else:
+            assert got[q] == cands[0] if cands[0] % 2 == 0 else cands[1], q
+    assert m.key_bits == 7
+    assert got[:4].tolist() == [0x3F80, 0x3F82, 0xBF80, 0x4000]
+    with pytest.raises(H.HgpError):
+        H.hgp_model_from_params(p, 21)

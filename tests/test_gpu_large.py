@@ -105,8 +105,10 @@ def test_learned_order_on_the_256k_snn():
         pair, score, key = (G.level_array(0, w) for w in (H.HGP_LEVEL_PAIR, H.HGP_LEVEL_SCORE,
                                                            H.HGP_LEVEL_KEY))
         match = G.level_array(0, H.HGP_LEVEL_MATCH)
-        model, _ = H.train_model(synth.training_graphs(2, 100), 1 << 10, 1 << 12, seed=0,
-                                 per_node=16, steps=1000, batch=4096, key_bits=6)
+        # the bench's training run (deterministic): 4 seeded 16k-node graphs, 2,000 steps
+        model, _ = H.train_model(synth.training_graphs(4, 100, sizes=(16384,)), 1 << 10, 1 << 12,
+                                 seed=0, per_node=16, steps=2000, batch=4096, lr=3e-3, key_bits=6,
+                                 init_params=synth.initial_params(0))
         res = G.partition(1 << 10, 1 << 12, model=model)
     check_matching(pair, match)
     nodes = np.random.default_rng(99).choice(g.num_nodes, size=48, replace=False).astype(np.int32)

@@ -80,6 +80,17 @@ def test_learned_hash_tables_and_no_refinement():
     compare_learned(g, 20, 80, synth.random_model(7, 0.5, 6), passes=0)
 
 
+@pytest.mark.parametrize("make,omega,delta,mseed", [
+    (lambda: synth.random_snn(700, 12, 8), 20, 80, 8),
+    (lambda: synth.snn_2k(0), 128, 512, 9),
+    (_weighted, 30, 90, 10)])
+def test_learned_cluster_path(make, omega, delta, mseed):
+    """The 8-CTA cluster scorer (packed 16-bit hist / inter in distributed
+    shared memory), forced at every level."""
+    compare_learned(make(), omega, delta, synth.random_model(mseed, 0.5, 6),
+                    debug=H.HGP_DEBUG_FORCE_CLUSTER)
+
+
 def test_zero_model_equals_the_plain_path():
     g = synth.random_snn(1200, 24, 6)
     with hgp.Graph.from_hypergraph(g) as G:
