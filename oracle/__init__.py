@@ -57,6 +57,7 @@ def _load():
             lib = ctypes.CDLL(build())
             vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
             lib.orun_create.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+            lib.orun_create_incident.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
             lib.orun_destroy.argtypes = [vp]
             lib.orun_partition.argtypes = [vp, i64, i64, i32]
             for name, rt in [("orun_num_levels", i32), ("orun_top_is_gamma", i32), ("orun_K", i32),
@@ -90,6 +91,8 @@ def _load():
             lib.orun_learn_samples.argtypes = [vp, vp, u64, i32, vp, vp, vp]
             lib.orun_score0_learned_nodes.argtypes = [vp, i64, i64, vp, vp, vp, u16, i32, vp, i32,
                                                       vp, vp, vp]
+            lib.orun_fill_baseline.argtypes = [vp, i64, i64, vp]
+            lib.orun_fill_baseline.restype = i32
             lib.oracle_splitmix64_at.argtypes = [u64, u64]
             lib.oracle_splitmix64_at.restype = u64
             lib.oracle_train_step.argtypes = [vp, vp, vp, i64, f64, f64, f64, f64, i32, vp, vp,
@@ -119,20 +122,23 @@ class Run:
     """One input hypergraph held by the oracle; ``partition`` runs the method
     and keeps every level's arrays for inspection."""
 
-    def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None):
+    def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None,
+                 incident=False):
+        """incident=True: Delta counts every incident hyperedge (in(n) = I(n))."""
         lib = _load()
         self._keep = [_i32(offsets), _i32(pins), _i32(node_weights), _i32(edge_weights)]
         h = ctypes.c_void_p()
-        rc = lib.orun_create(int(num_nodes), int(len(offsets) - 1), *[_p(a) for a in self._keep],
-                             ctypes.byref(h))
+        create = lib.orun_create_incident if incident else lib.orun_create
+        rc = create(int(num_nodes), int(len(offsets) - 1), *[_p(a) for a in self._keep],
+                    ctypes.byref(h))
         if rc:
             raise OracleError(rc, "create")
         self._h = h
         self.num_nodes = int(num_nodes)
 
     @classmethod
-    def from_graph(cls, g):
-        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights)
+    def from_graph(cls, g, incident=False):
+        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, incident)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -190,6 +196,14 @@ class Run:
         if rc:
             raise OracleError(rc, "score0_learned_nodes")
         return tuple(out)
+
+    def fill_baseline(self, omega, delta):
+        """The constraint-only baseline: (part ids, number of parts)."""
+        ids = np.empty(self.num_nodes, dtype=np.int32)
+        k = _load().orun_fill_baseline(self._h, int(omega), int(delta), _p(ids))
+        if k < 0:
+            raise OracleError(-k, "fill_baseline")
+        return ids, int(k)
 
     def features0(self, n, m):
         x = np.empty(8, dtype=np.float32)

@@ -101,7 +101,7 @@ static int transpose(int32_t rows, int32_t cols, const int64_t *off,
  */
 static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
                         const int32_t *pins, const int32_t *nw, const int32_t *ew,
-                        olevel *g, int32_t **src_out) {
+                        int32_t incident, olevel *g, int32_t **src_out) {
     if (N < 1 || E < 0 || !offsets || (E > 0 && !pins)) return ORC_INVALID;
     if (offsets[0] != 0) return ORC_INVALID;
     for (int32_t e = 0; e < E; ++e)
@@ -135,7 +135,9 @@ static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
     }
     int rc = transpose(E, N, g->poff, g->pins, &g->ioff, &g->inc);
     if (rc) { free(src); olevel_free(g); return rc; }
-    /* in(n): the same transpose restricted to destination pins. */
+    /* in(n): the same transpose restricted to destination pins.  With
+     * `incident` (the Delta variant that counts every incident hyperedge,
+     * which the paper calls a trivial generalisation) in(n) = I(n). */
     int64_t *dcount = (int64_t *)calloc((size_t)E + 1, sizeof(int64_t));
     int32_t *dst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P > 0 ? P : 1));
     if (!dcount || !dst) { free(dcount); free(dst); free(src); olevel_free(g); return ORC_OOM; }
@@ -143,7 +145,7 @@ static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
     for (int32_t e = 0; e < E; ++e) {
         dcount[e] = k;
         for (int64_t j = g->poff[e]; j < g->poff[e + 1]; ++j)
-            if (g->pins[j] != src[e]) dst[k++] = g->pins[j];
+            if (incident || g->pins[j] != src[e]) dst[k++] = g->pins[j];
     }
     dcount[E] = k;
     rc = transpose(E, N, dcount, dst, &g->noff, &g->in);
@@ -835,8 +837,24 @@ static void orun_clear(orun *r) {
     r->nlev = 1; r->done = 0; r->num_parts = 0; r->cost = 0;   /* level 0 always exists */
 }
 
+static int orun_create_mode(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
+                            const int32_t *node_w, const int32_t *edge_w, int32_t incident,
+                            orun **out);
+
 int orun_create(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
                 const int32_t *node_w, const int32_t *edge_w, orun **out) {
+    return orun_create_mode(N, E, offsets, pins, node_w, edge_w, 0, out);
+}
+
+/* Delta counting every incident hyperedge instead of the inbound ones. */
+int orun_create_incident(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
+                         const int32_t *node_w, const int32_t *edge_w, orun **out) {
+    return orun_create_mode(N, E, offsets, pins, node_w, edge_w, 1, out);
+}
+
+static int orun_create_mode(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
+                            const int32_t *node_w, const int32_t *edge_w, int32_t incident,
+                            orun **out) {
     orun *r = (orun *)calloc(1, sizeof(orun));
     if (!r) return ORC_OOM;
     if (N < 1) { free(r); return ORC_INVALID; }
@@ -852,7 +870,7 @@ int orun_create(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pin
     r->rt = (rtrace *)calloc((size_t)r->cap, sizeof(rtrace));
     int rc = ORC_OOM;
     if (r->G && r->pair && r->score && r->match && r->gamma && r->rho_in && r->rho_out && r->key && r->rt)
-        rc = build_level0(N, E, offsets, pins, node_w, edge_w, &r->G[0], &r->src);
+        rc = build_level0(N, E, offsets, pins, node_w, edge_w, incident, &r->G[0], &r->src);
     if (!rc) {
         r->in_off = (int32_t *)malloc(sizeof(int32_t) * ((size_t)E + 1));
         r->in_pins = (int32_t *)malloc(sizeof(int32_t) * (size_t)(offsets[E] > 0 ? offsets[E] : 1));
@@ -1475,4 +1493,43 @@ int orun_score0_learned_nodes(const orun *r, int64_t omega, int64_t delta, const
                            touched, stamp);
     free(hist); free(touched); free(stamp);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Constraint-only baseline (the paper's one-pass comparison, Sec. V). */
+/* ------------------------------------------------------------------ */
+/*
+ * Nodes are taken in id order and appended to the current part while both
+ * bounds hold: w(part) + w(n) <= Omega and |in(part) u in(n)| <= Delta;
+ * otherwise n opens the next part.  Reading: this is the paper's baseline
+ * that fills partitions one at a time in node order, with no regard to
+ * connectivity.  Parts are numbered in opening order.
+ * Returns the number of parts (or a negative ORC_ code).
+ */
+int32_t orun_fill_baseline(const orun *r, int64_t omega, int64_t delta, int32_t *part_ids) {
+    const olevel *g = &r->G[0];
+    if (omega < 1 || delta < 0) return -ORC_INVALID;
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!stamp) return -ORC_OOM;
+    for (int32_t e = 0; e < g->E; ++e) stamp[e] = -1;
+    int32_t p = -1;
+    int64_t w = 0, u = 0;
+    for (int32_t n = 0; n < g->V; ++n) {
+        if (g->w[n] > omega || g->noff[n + 1] - g->noff[n] > delta) { free(stamp); return -ORC_INFEASIBLE; }
+        int64_t fresh = 0;
+        if (p >= 0)
+            for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) fresh += stamp[g->in[j]] != p;
+        if (p < 0 || w + g->w[n] > omega || u + fresh > delta) {
+            p++;
+            w = 0;
+            u = 0;
+            fresh = g->noff[n + 1] - g->noff[n];
+        }
+        for (int64_t j = g->noff[n]; j < g->noff[n + 1]; ++j) stamp[g->in[j]] = p;
+        w += g->w[n];
+        u += fresh;
+        part_ids[n] = p;
+    }
+    free(stamp);
+    return p + 1;
 }

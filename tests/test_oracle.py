@@ -424,3 +424,109 @@ def test_infeasible_singleton():
         r.partition(4, 2)
     assert ei.value.code == oracle.INFEASIBLE
     assert r.partition(4, 3).num_parts >= 1
+
+
+# ---------------------------------------------------------------- fill baseline
+@pytest.mark.parametrize("seed,omega,delta", [(0, 6, 30), (1, 10, 60), (2, 3, 200), (3, 50, 25)])
+def test_fill_baseline_definition(seed, omega, delta):
+    """Constraint-only baseline: parts are consecutive id ranges, each
+    feasible, and each range's successor node would break a bound if added."""
+    g = synth.random_snn(300, 8, seed, size_max=14)
+    ins = in_sets(g.num_nodes, g.offsets, g.pins)
+    if max(len(s) for s in ins) > delta:
+        pytest.skip("a single node exceeds delta")
+    with oracle.Run.from_graph(g) as r:
+        ids, k = r.fill_baseline(omega, delta)
+    assert ids[0] == 0 and np.all(np.diff(ids) >= 0) and np.all(np.diff(ids) <= 1)
+    assert ids[-1] == k - 1
+    st = part_stats(g.num_nodes, g.offsets, g.pins, ids)
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    for p in range(k - 1):
+        members = np.nonzero(ids == p)[0]
+        nxt = members[-1] + 1
+        u = set().union(*(ins[n] for n in members))
+        assert len(members) + 1 > omega or len(u | ins[nxt]) > delta
+
+
+def test_fill_baseline_closed_forms():
+    g = synth.random_snn(100, 5, 1)
+    with oracle.Run.from_graph(g) as r:
+        ids, k = r.fill_baseline(1, 10_000)          # every node alone
+        assert k == 100 and ids.tolist() == list(range(100))
+        ids, k = r.fill_baseline(100, 10_000)        # everything in one part
+        assert k == 1 and not ids.any()
+        ids, k = r.fill_baseline(7, 10_000)          # Omega alone decides: blocks of 7
+        assert ids.tolist() == [n // 7 for n in range(100)]
+
+
+# ---------------------------------------------------------------- incident Delta
+def _incident_stats(g, rho):
+    """{part: (node count, |union of I(n)|)} from Python sets."""
+    eds = edges_of(g.offsets, g.pins)
+    inc = [set() for _ in range(g.num_nodes)]
+    for e, ed in enumerate(eds):
+        for v in ed:
+            inc[v].add(e)
+    st = {}
+    for n in range(g.num_nodes):
+        w, s = st.get(int(rho[n]), (0, set()))
+        st[int(rho[n])] = (w + 1, s | inc[n])
+    return {p: (w, len(s)) for p, (w, s) in st.items()}
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_incident_mode_counts_every_incident_hyperedge(seed):
+    g = synth.random_snn(400, 10, seed, size_max=16)
+    omega, delta = 16, 60
+    with oracle.Run.from_graph(g, incident=True) as r:
+        res = r.partition(omega, delta)
+    st = _incident_stats(g, res.part_ids)
+    assert sorted(st) == list(range(res.num_parts))
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    assert [st[p][1] for p in range(res.num_parts)] == res.part_inbound.tolist()
+    assert conn(g.offsets, g.pins, res.part_ids) == res.cost
+
+
+def test_incident_mode_equals_inbound_mode_when_delta_never_binds():
+    g = synth.random_snn(500, 12, 4)
+    a = oracle.partition(g, 20, 10 ** 6)
+    with oracle.Run.from_graph(g, incident=True) as r:
+        b = r.partition(20, 10 ** 6)
+    assert np.array_equal(a.part_ids, b.part_ids) and a.cost == b.cost
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_incident_mode_exhaustive(seed):
+    """Tiny graphs: feasible under the incident count, never below the optimum
+    found by enumerating every set partition."""
+    rng = np.random.default_rng(50 + seed)
+    N = 7
+    off, pins = [0], []
+    for _ in range(5):
+        k = int(rng.integers(2, 4))
+        pins += rng.choice(N, size=k, replace=False).tolist()
+        off.append(len(pins))
+    g = synth.Hypergraph(N, np.array(off, np.int32), np.array(pins, np.int32))
+    omega, delta = 3, 4
+    # brute force over all set partitions with the incident-hyperedge count
+    best = None
+    for rho in __import__("brute").set_partitions(N):
+        st = _incident_stats(g, np.array(rho))
+        if all(w <= omega and d <= delta for w, d in st.values()):
+            c = conn(g.offsets, g.pins, rho)
+            best = c if best is None or c < best else best
+    with oracle.Run.from_graph(g, incident=True) as r:
+        if best is None:
+            with pytest.raises(oracle.OracleError):
+                r.partition(omega, delta)
+            return
+        try:
+            res = r.partition(omega, delta)
+        except oracle.OracleError:
+            # only possible when a single node alone breaks the incident bound
+            assert any(len([e for e, ed in enumerate(edges_of(g.offsets, g.pins)) if n in ed]) > delta
+                       for n in range(N))
+            return
+    st = _incident_stats(g, res.part_ids)
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    assert res.cost >= best
