@@ -348,14 +348,21 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
                          if sc_ms > 0 else 0.0}}
 
 
-LEARNED256K_WORKLOAD = ("learned candidate order on a random SNN hypergraph, 262,144 nodes, one "
-                        "hyperedge per node of 256 pins, 67,108,864 pins, int32 CSR, Omega=2^10, "
-                        "Delta=2^12, seed 0; model trained on 4 seeded 16,384-node graphs")
+LEARNED_LARGE = {
+    "learned256k": ("learned candidate order on a random SNN hypergraph, 262,144 nodes, one "
+                    "hyperedge per node of 256 pins, 67,108,864 pins, int32 CSR, Omega=2^10, "
+                    "Delta=2^12, seed 0; model trained on 4 seeded 16,384-node graphs",
+                    "snn_256k", 1 << 10, 1 << 12),
+    "learnedconv200k": ("learned candidate order on a layered conv-style SNN hypergraph, 8 layers x "
+                        "16x16 x 100 channels (204,800 nodes), 3x3 windows on 88..100 channels, "
+                        "~1.4e8 pins, int32 CSR, Omega=2^12, Delta=2^16, seed 0; model trained on 4 "
+                        "seeded 16,384-node random SNN graphs", "conv_200k", 1 << 12, 1 << 16),
+}
 
 
-def run_learned256k(args, rank, world):
-    """The learned order on the 262,144-node SNN: train (untimed), then time
-    whole partitions (create + partition + destroy, device-resident inputs)."""
+def run_learned_large(args, rank, world):
+    """The learned order on a large workload: train (untimed), then time whole
+    partitions (create + partition + destroy, device-resident inputs)."""
     import torch
     import synth
     from paper_2604_14411_gb300 import hgp as H
@@ -374,7 +381,8 @@ def run_learned256k(args, rank, world):
                                   batch=LEARN_BATCH, lr=LEARN_LR, key_bits=LEARN_KEY_BITS,
                                   init_params=synth.initial_params(0), stream=stream)
     train_s = time.perf_counter() - t0
-    g = synth.snn_256k(0)
+    desc, make, omega, delta = LEARNED_LARGE[args.workload]
+    g = getattr(synth, make)(0)
     N, P = g.num_nodes, g.num_pins
     d_off = torch.from_numpy(g.offsets.copy()).to(dev)
     d_pins = torch.from_numpy(g.pins.copy()).to(dev)
@@ -384,7 +392,7 @@ def run_learned256k(args, rank, world):
     def step(debug=0):
         h = H.hgp_create(N, d_off, d_pins, stream=stream)
         try:
-            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, None, None, 1, debug, 0, model)
+            res = H.hgp_partition(h, omega, delta, d_ids, None, None, 1, debug, 0, model)
             st = H.hgp_get_stats(h)
         finally:
             H.hgp_destroy(h)
@@ -414,14 +422,14 @@ def run_learned256k(args, rank, world):
     clocks = sampler.stop(local)
     job = job_time_ms(sum(times), dist, dev)
     ids = d_ids.cpu().numpy()
-    cost, feasible = recount(g, ids, OMEGA, DELTA)
+    cost, feasible = recount(g, ids, omega, delta)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": job_value(P, args.steps, world, job), "unit": "pins/s",
             "n_gpus": world, "steps": args.steps, "warmup": warm, "ms_per_step": job / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": LEARNED256K_WORKLOAD, "omega": OMEGA, "delta": DELTA, "pins": P,
+            "config": {"workload": desc, "omega": omega, "delta": delta, "pins": P,
                        "l2": "flushed between timed steps (256 MB write)"},
             "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
             "coarsening_pins_per_s": P / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
@@ -444,10 +452,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="snn16k", choices=["snn16k", "batch64", "learned256k"],
+    ap.add_argument("--workload", default="snn16k",
+                    choices=["snn16k", "batch64", "learned256k", "learnedconv200k"],
                     help="snn16k: the default single-hypergraph workload; batch64: 64 uneven "
-                         "hypergraphs through hgp_partition_batch; learned256k: the learned order "
-                         "on the 262,144-node SNN (the last two print their own JSON line)")
+                         "hypergraphs through hgp_partition_batch; learned256k / learnedconv200k: "
+                         "the learned order on the 262,144-node SNN / the 204,800-node conv-style "
+                         "SNN (these print their own JSON line)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-order leg (training + timed learned partitions)")
     ap.add_argument("--save-model", default=None,
@@ -467,8 +477,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch64":
         return run_batch(args, rank, world)
-    if args.workload == "learned256k":
-        return run_learned256k(args, rank, world)
+    if args.workload in ("learned256k", "learnedconv200k"):
+        return run_learned_large(args, rank, world)
 
     import torch
     import synth
@@ -566,6 +576,13 @@ def main():
     learned = None
     if not args.no_learned:
         learned = learned_leg(args, step, flush, stream, g, d_ids, res[0], statistics.median(times), H)
+    # quality floor: the constraint-only comparison (parts filled in node-id order)
+    with H.Graph(N, d_off, d_pins, stream=stream) as G:
+        fill = G.fill_baseline(OMEGA, DELTA)
+    quality = {"fill_baseline_cost": fill.cost, "fill_baseline_parts": fill.num_parts,
+               "plain_cost_vs_fill": res[0] / fill.cost}
+    if learned is not None:
+        quality["learned_cost_vs_fill"] = learned["cost"] / fill.cost
 
     st = stats[-1]
     peak, peak_kind = load_peaks()
@@ -612,6 +629,7 @@ def main():
         }
         if learned is not None:
             line["learned"] = learned
+        line["quality"] = quality
         if not args.no_cpu_baseline:
             v, ts = oracle_sample(steps=3)
             line["cpu_baseline"] = {"value": v, "unit": "pins/s", "cores": 1, "kind": "oracle",

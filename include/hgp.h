@@ -52,6 +52,9 @@ typedef enum {
 
 /* hgp_create flags */
 #define HGP_INPUT_DEVICE 1u    /* offsets/pins/weights are device pointers */
+#define HGP_DELTA_INCIDENT 4u  /* hgp_create: Delta bounds the distinct hyperedges incident to a part
+                                  (in(n) = I(n)) instead of the inbound ones; the paper notes the
+                                  generalisation in Sec. II-A */
 
 /* hgp_result.out_flags */
 #define HGP_OUTPUT_DEVICE 1u   /* part_ids/part_weight/part_inbound are device pointers */
@@ -82,7 +85,8 @@ typedef struct hgp_graph hgp_graph;
  *                 their sum must be < 2^31
  *   edge_weights  [num_edges] int32 >= 1, or NULL for unit weights (omega);
  *                 their sum must be < 2^31
- *   flags         HGP_INPUT_DEVICE: the four arrays are device memory
+ *   flags         HGP_INPUT_DEVICE: the four arrays are device memory;
+ *                 HGP_DELTA_INCIDENT: Delta counts incident, not inbound, hyperedges
  *                 readable on `stream`; otherwise host memory
  *   stream        cudaStream_t to run on (NULL = default stream)
  *   out           receives the handle
@@ -225,6 +229,15 @@ enum {
 int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which);
 /* Copies array `which` of level l into host buffer out (int64 elements). */
 int hgp_get_level_array(const hgp_graph *g, int32_t level, int32_t which, int64_t *out);
+
+/*
+ * The constraint-only comparison of the paper's evaluation (Sec. V): nodes in
+ * id order are appended to the current part while w(part) + w(n) <= omega and
+ * |in(part) u in(n)| <= delta, otherwise they open the next part.  res as
+ * for hgp_partition (num_levels = 0); parts are numbered in opening order.
+ * Same errors as hgp_partition.  A quality floor to compare costs with.
+ */
+int hgp_fill_baseline(hgp_graph *g, int64_t omega, int64_t delta, hgp_result *res);
 
 /*
  * Training pairs for the learned order, labelled by a partition of the

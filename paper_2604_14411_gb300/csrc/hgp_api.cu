@@ -1,6 +1,7 @@
 // C ABI of the library (include/hgp.h): handle lifetime, the level loop of
 // Sec. II-B (coarsen until ceil(W / Omega) nodes or no merge, then refine
 // from the coarsest level down while projecting), and result delivery.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -23,6 +24,8 @@ bool model_valid(const hgp_model *m);
 cudaError_t run_learn_samples(const Level &L0, const int32_t *ew, const int32_t *part_ids,
                               uint64_t seed, int32_t per_node, float *x, float *y,
                               int32_t *partner, cudaStream_t s);
+cudaError_t run_fill_baseline(Arena &ar, const Level &L0, int64_t omega, int64_t delta,
+                              int32_t *part, int32_t *d_nparts, cudaStream_t s);
 cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
                       const int32_t *key, int32_t *match, int32_t *gamma, int32_t *d_V2,
                       int32_t *status, cudaStream_t s);
@@ -113,7 +116,7 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     *out = nullptr;
     if (num_nodes < 1 || num_edges < 0 || !offsets || (num_edges > 0 && !pins))
         return HGP_ERR_INVALID_ARG;
-    if ((flags & ~HGP_INPUT_DEVICE) != 0) return HGP_ERR_INVALID_ARG;
+    if ((flags & ~(HGP_INPUT_DEVICE | HGP_DELTA_INCIDENT)) != 0) return HGP_ERR_INVALID_ARG;
     double t0 = now_ms();
     int64_t launches0 = g_launches;
     hgp_graph *g = new (std::nothrow) hgp_graph();
@@ -178,6 +181,14 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     cudaError_t ce = cudaSuccess;
     std::string why;
     int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, &g->wsum_e, &ce, &why, s);
+    if (rc == 0 && (flags & HGP_DELTA_INCIDENT)) {
+        // Delta counts every incident hyperedge: in(n) = I(n), and every pin
+        // (the source's node included) is a destination at every level
+        L.noff = L.ioff;
+        L.inn = L.inc;
+        L.Q = L.P;
+        if (num_edges > 0) CKC(cudaMemsetAsync(L.sdst, 1, (size_t)num_edges, s), "incident flags");
+    }
     if (rc != 0) {
         tmp.release_all();
         if (rc < 0) return bail(cuda_fail(g, ce, "build level 0"));
@@ -545,6 +556,57 @@ extern "C" int hgp_partition(hgp_graph *g, int64_t omega, int64_t delta, const h
     return partition_on(g, omega, delta, opt, res, g->stream);
 }
 
+// The paper's constraint-only comparison: parts filled in node-id order.
+extern "C" int hgp_fill_baseline(hgp_graph *g, int64_t omega, int64_t delta, hgp_result *res) {
+    if (!g || !res) return HGP_ERR_INVALID_ARG;
+    if (omega < 1 || delta < 0) return fail(g, HGP_ERR_INVALID_ARG, "omega must be >= 1 and delta >= 0");
+    if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
+    if (g->max_w > omega || g->max_in > delta)
+        return fail(g, HGP_ERR_INFEASIBLE, "a single node exceeds omega or delta; no partition exists");
+    cudaStream_t s = g->stream;
+    Arena tmp;
+    tmp.stream = s;
+    auto done = [&](cudaError_t e, const char *where) {
+        cudaStreamSynchronize(s);
+        tmp.release_all();
+        cudaStreamSynchronize(s);
+        return e ? cuda_fail(g, e, where) : HGP_OK;
+    };
+    const bool outdev = (res->out_flags & HGP_OUTPUT_DEVICE) != 0;
+    const int32_t N = g->N;
+    int32_t *rho = nullptr, *d_np = nullptr, *d_ids = outdev ? res->part_ids : nullptr;
+    int64_t *d_pw = outdev ? res->part_weight : nullptr;
+    int32_t *d_pin = outdev ? res->part_inbound : nullptr;
+    unsigned long long *d_cost = nullptr;
+    cudaError_t e = dalloc(tmp, &rho, N);
+    if (!e) e = dalloc(tmp, &d_np, 2);
+    if (!e) e = dalloc(tmp, &d_cost, 1);
+    if (!e && !outdev) e = dalloc(tmp, &d_ids, N);
+    if (!e && !outdev && res->part_weight) e = dalloc(tmp, &d_pw, N);
+    if (!e && !outdev && res->part_inbound) e = dalloc(tmp, &d_pin, N);
+    if (!e) e = run_fill_baseline(tmp, g->L0, omega, delta, rho, d_np, s);
+    int32_t K = 0;
+    if (!e) e = cudaMemcpyAsync(&K, d_np, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e) e = run_finalize(tmp, g->L0, g->ew, rho, K > 0 ? K : 1, d_ids, d_pw, d_pin, d_cost, d_np + 1, s);
+    unsigned long long cost = 0;
+    int32_t np = 0;
+    if (!e) e = cudaMemcpyAsync(&cost, d_cost, sizeof(cost), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&np, d_np + 1, sizeof(np), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e && !outdev) {
+        e = cudaMemcpyAsync(res->part_ids, d_ids, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, s);
+        if (!e && res->part_weight)
+            e = cudaMemcpyAsync(res->part_weight, d_pw, sizeof(int64_t) * (size_t)np, cudaMemcpyDeviceToHost, s);
+        if (!e && res->part_inbound)
+            e = cudaMemcpyAsync(res->part_inbound, d_pin, sizeof(int32_t) * (size_t)np, cudaMemcpyDeviceToHost, s);
+    }
+    res->cost = (int64_t)cost;
+    res->num_parts = np;
+    res->num_levels = 0;
+    return done(e, "fill baseline");
+}
+
 // Many handles at once: worker threads take instances from a shared counter
 // and run each on a stream of their own, so the small per-level kernels and
 // host round trips of different instances overlap on the GPU.  Every
@@ -557,6 +619,9 @@ extern "C" int hgp_partition_batch(hgp_graph *const *gs, int32_t count, const in
         if (!gs[i]) return HGP_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HGP_ERR_CUDA;
+    // Instances are taken in index order.  (Largest-first ordering was tried:
+    // it starts the biggest instances together, and their per-level storage
+    // exhausted device memory on the 64-instance workload.)
     int workers = count < 16 ? count : 16;
     std::atomic<int32_t> next(0);
     std::vector<int> rc(count > 0 ? count : 1, HGP_OK);

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libhgp.so")
 HGP_OK, HGP_ERR_INVALID_ARG, HGP_ERR_INFEASIBLE, HGP_ERR_OOM = 0, 1, 2, 3
 HGP_ERR_CUDA, HGP_ERR_DEVICE_LIMIT, HGP_ERR_STATE, HGP_ERR_SCRATCH_LIMIT = 4, 5, 6, 7
 HGP_INPUT_DEVICE = 1
+HGP_DELTA_INCIDENT = 4
 HGP_OUTPUT_DEVICE = 1
 HGP_DEBUG_KEEP_LEVELS = 1
 HGP_DEBUG_TIMING = 2
@@ -115,7 +116,7 @@ class hgp_stats(ctypes.Structure):
 EXPORTS = ("hgp_create", "hgp_partition", "hgp_get_stats", "hgp_get_level_len",
            "hgp_get_level_array", "hgp_error_string", "hgp_last_error", "hgp_destroy",
            "hgp_score_noalloc", "hgp_partition_batch", "hgp_learn_samples", "hgp_train_mlp",
-           "hgp_model_from_params")
+           "hgp_model_from_params", "hgp_fill_baseline")
 
 _lib = None
 
@@ -154,6 +155,8 @@ def load(path: str = LIB_PATH):
     lib.hgp_train_mlp.restype = ctypes.c_int
     lib.hgp_model_from_params.argtypes = [vp, i32, ctypes.POINTER(hgp_model)]
     lib.hgp_model_from_params.restype = ctypes.c_int
+    lib.hgp_fill_baseline.argtypes = [vp, i64, i64, ctypes.POINTER(hgp_result)]
+    lib.hgp_fill_baseline.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -190,9 +193,11 @@ def _check(rc, handle=None):
         raise HgpError(rc, msg)
 
 
-def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None):
+def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None,
+               incident=False):
     """hgp_create: returns an opaque handle.  Arrays are all host numpy int32 or
-    all torch int32 CUDA tensors."""
+    all torch int32 CUDA tensors.  incident=True: Delta counts every incident
+    hyperedge (HGP_DELTA_INCIDENT)."""
     lib = load()
     dev = _is_device(offsets)
     arrs = [offsets, pins, node_weights, edge_weights]
@@ -204,8 +209,9 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
                 raise TypeError("device inputs must be contiguous torch.int32 CUDA tensors")
     h = ctypes.c_void_p()
     E = int(arrs[0].shape[0]) - 1
+    flags = (HGP_INPUT_DEVICE if dev else 0) | (HGP_DELTA_INCIDENT if incident else 0)
     rc = lib.hgp_create(int(num_nodes), E, *[_ptr(a) for a in arrs],
-                        HGP_INPUT_DEVICE if dev else 0, _stream_handle(stream), ctypes.byref(h))
+                        flags, _stream_handle(stream), ctypes.byref(h))
     _check(rc, None)
     return h
 
@@ -324,13 +330,14 @@ class Result:
 class Graph:
     """Owning wrapper around an hgp_graph handle."""
 
-    def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None):
+    def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None,
+                 incident=False):
         self.num_nodes = int(num_nodes)
-        self._h = hgp_create(num_nodes, offsets, pins, node_weights, edge_weights, stream)
+        self._h = hgp_create(num_nodes, offsets, pins, node_weights, edge_weights, stream, incident)
 
     @classmethod
-    def from_hypergraph(cls, g, stream=None):
-        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream)
+    def from_hypergraph(cls, g, stream=None, incident=False):
+        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream, incident)
 
     def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)
@@ -344,6 +351,18 @@ class Graph:
                          refine_passes=1, debug=0, model=None):
         return hgp_partition(self._h, omega, delta, part_ids, part_weight, part_inbound,
                              refine_passes, debug, 0, model)
+
+    def fill_baseline(self, omega, delta) -> Result:
+        """hgp_fill_baseline: parts filled in node-id order (constraint-only)."""
+        ids = np.empty(self.num_nodes, dtype=np.int32)
+        pw = np.empty(self.num_nodes, dtype=np.int64)
+        pin = np.empty(self.num_nodes, dtype=np.int32)
+        res = hgp_result()
+        res.part_ids, res.part_weight, res.part_inbound = ids.ctypes.data, pw.ctypes.data, pin.ctypes.data
+        res.out_flags = 0
+        _check(load().hgp_fill_baseline(self._h, int(omega), int(delta), ctypes.byref(res)), self._h)
+        k = int(res.num_parts)
+        return Result(ids, int(res.cost), k, 0, pw[:k], pin[:k])
 
     def learn_samples(self, part_ids, seed, per_node, with_partner=True):
         """hgp_learn_samples into new torch CUDA tensors: (x [S, 8], y [S],

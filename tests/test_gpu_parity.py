@@ -36,10 +36,10 @@ TRACE = [(H.HGP_LEVEL_PAIR, oracle.A_PAIR), (H.HGP_LEVEL_SCORE, oracle.A_SCORE),
          (H.HGP_LEVEL_RHO_IN, oracle.A_RHO_IN), (H.HGP_LEVEL_RHO_OUT, oracle.A_RHO_OUT)]
 
 
-def compare(g, omega, delta, passes=1, debug=0, trace=True):
-    with oracle.Run.from_graph(g) as r:
+def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False):
+    with oracle.Run.from_graph(g, incident=incident) as r:
         want = r.partition(omega, delta, passes)
-        with hgp.Graph.from_hypergraph(g) as G:
+        with hgp.Graph.from_hypergraph(g, incident=incident) as G:
             got = G.partition(omega, delta, passes,
                               debug=(H.HGP_DEBUG_KEEP_LEVELS if trace else 0) | debug)
             assert got.num_levels == r.num_levels
@@ -104,12 +104,16 @@ def test_conv_style():
     compare(synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400)
 
 
-def test_weighted():
+def _weighted_graph():
     g = synth.random_snn(600, 10, 11)
     rng = np.random.default_rng(5)
     g.node_weights = rng.integers(1, 4, size=600).astype(np.int32)
     g.edge_weights = rng.integers(1, 7, size=g.num_edges).astype(np.int32)
-    compare(g, 30, 90)
+    return g
+
+
+def test_weighted():
+    compare(_weighted_graph(), 30, 90)
 
 
 @pytest.mark.parametrize("debug", [H.HGP_DEBUG_FORCE_GLOBAL, H.HGP_DEBUG_NO_BITMAP,
@@ -236,3 +240,48 @@ def test_stored_expected(name, make):
     assert conn(g.offsets, g.pins, res.part_ids) == res.cost
     st = part_stats(g.num_nodes, g.offsets, g.pins, res.part_ids)
     assert all(w <= int(exp["omega"]) and d <= int(exp["delta"]) for w, d in st.values())
+
+
+@pytest.mark.parametrize("make,omega,delta", [
+    (lambda: synth.random_snn(300, 9, 3), 10, 40),
+    (lambda: synth.random_snn(2000, 16, 4, size_max=40), 64, 400),
+    (_weighted_graph, 30, 90),
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400),
+    (lambda: synth.snn_16k(0), 1024, 4096)])
+def test_fill_baseline_bitexact(make, omega, delta):
+    """The constraint-only comparison (parts filled in node-id order), up to
+    the bench workload at full size."""
+    g = make()
+    with oracle.Run.from_graph(g) as r:
+        ids, k = r.fill_baseline(omega, delta)
+    with hgp.Graph.from_hypergraph(g) as G:
+        res = G.fill_baseline(omega, delta)
+    assert np.array_equal(res.part_ids, ids) and res.num_parts == k
+    assert res.cost == conn(g.offsets, g.pins, ids, g.edge_weights)
+    st = part_stats(g.num_nodes, g.offsets, g.pins, ids, g.node_weights)
+    assert [st[p][0] for p in range(k)] == res.part_weight.tolist()
+    assert [st[p][1] for p in range(k)] == res.part_inbound.tolist()
+
+
+@pytest.mark.parametrize("make,omega,delta", [
+    (lambda: synth.random_snn(600, 10, 3), 16, 60),
+    (lambda: synth.snn_2k(0), 128, 1024),
+    (_weighted_graph, 30, 150),
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 600)])
+def test_incident_mode_bitexact(make, omega, delta):
+    """Delta counting every incident hyperedge (HGP_DELTA_INCIDENT)."""
+    compare(make(), omega, delta, incident=True)
+
+
+def test_incident_mode_learned_and_fill():
+    g = synth.random_snn(900, 12, 5)
+    model = synth.random_model(21, 0.5, 6)
+    with oracle.Run.from_graph(g, incident=True) as r:
+        want = r.partition_learned(20, 120, model)
+        ids, k = r.fill_baseline(20, 120)
+    with hgp.Graph.from_hypergraph(g, incident=True) as G:
+        got = G.partition(20, 120, model=model)
+        fill = G.fill_baseline(20, 120)
+    assert np.array_equal(got.part_ids, want.part_ids) and got.cost == want.cost
+    assert np.array_equal(got.part_inbound, want.part_inbound)
+    assert np.array_equal(fill.part_ids, ids) and fill.num_parts == k
