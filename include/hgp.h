@@ -223,7 +223,8 @@ enum {
     HGP_LEVEL_RHO_OUT = 5,     /* [V_l] partition after refinement */
     HGP_LEVEL_WEIGHT = 6,      /* [V_l] node weights */
     HGP_LEVEL_REFINE = 7,      /* [3] proposed moves, applied prefix, gain (as int64) */
-    HGP_LEVEL_KEY = 8          /* [V_l] learned order only: key(n, pair(n)), 0 when none */
+    HGP_LEVEL_KEY = 8,         /* [V_l] learned order only: key(n, pair(n)), 0 when none */
+    HGP_LEVEL_GAIN_SEQ = 9     /* [M] in-sequence gain of each sorted move (last pass) */
 };
 /* Length of array `which` of level l (-1 if absent). */
 int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which);

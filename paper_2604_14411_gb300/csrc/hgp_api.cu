@@ -37,7 +37,8 @@ int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, co
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            PropTiming *pt, const PropReuse &ru, cudaStream_t s);
+                            PropTiming *pt, const PropReuse &ru, std::vector<int32_t> *gseq_out,
+                            cudaStream_t s);
 void run_project(int32_t V, const int32_t *gamma, const int32_t *rho_c, int32_t *rho_f,
                  cudaStream_t s);
 cudaError_t run_finalize(Arena &tmp, const Level &L, const int32_t *ew, const int32_t *rho,
@@ -80,7 +81,7 @@ struct hgp_graph {
     int32_t max_w = 0, max_in = 0;
     std::string err;
     hgp_stats stats{};
-    std::vector<std::vector<int64_t>> dbg[9];
+    std::vector<std::vector<int64_t>> dbg[10];
 };
 
 static int fail(hgp_graph *g, int code, const std::string &msg) {
@@ -447,8 +448,16 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
                 ru.gamma = Lv.gamma;
                 ru.match = Lv.match;
             }
+            std::vector<int32_t> gs;
+            const bool keep_gs = (debug & HGP_DEBUG_KEEP_LEVELS) && p == passes - 1;
             CKP(run_refine_pass(tmp, Lv, g->ew, g->wsum_e, rho, K, omega, delta, d_rstat + 3 * l,
-                                d_applied, debug, tm.on ? &ptime : nullptr, ru, s), "refine");
+                                d_applied, debug, tm.on ? &ptime : nullptr, ru,
+                                keep_gs ? &gs : nullptr, s), "refine");
+            if (keep_gs) {
+                auto &vv = g->dbg[HGP_LEVEL_GAIN_SEQ];
+                if ((int)vv.size() <= l) vv.resize(l + 1);
+                vv[l].assign(gs.begin(), gs.end());
+            }
             tmp.reset();
         }
         if (debug & HGP_DEBUG_KEEP_LEVELS) {
@@ -660,7 +669,7 @@ extern "C" int hgp_get_stats(const hgp_graph *g, hgp_stats *st) {
 }
 
 extern "C" int64_t hgp_get_level_len(const hgp_graph *g, int32_t level, int32_t which) {
-    if (!g || which < 0 || which > HGP_LEVEL_KEY || level < 0) return -1;
+    if (!g || which < 0 || which > HGP_LEVEL_GAIN_SEQ || level < 0) return -1;
     const auto &vv = g->dbg[which];
     if (level >= (int)vv.size() || (vv[level].empty() && which != HGP_LEVEL_REFINE)) return -1;
     return (int64_t)vv[level].size();

@@ -755,7 +755,8 @@ __global__ void k_gain_flag(int32_t V, const int32_t *gain, int32_t *flag) {
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
-                            PropTiming *pt, const PropReuse &ru, cudaStream_t s) {
+                            PropTiming *pt, const PropReuse &ru, std::vector<int32_t> *gseq_out,
+                            cudaStream_t s) {
     int32_t V = L.V;
     int32_t *size, *inb;
     cudaError_t e = dalloc(tmp, &size, K);
@@ -1016,6 +1017,19 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     count_launch();
     k_apply<<<grid1d(M), 256, 0, s>>>(M, dk, mv_n, mv_pd, rho);
     count_launch();
+    if (gseq_out) {            // debug trace: the in-sequence gains of the sorted moves
+        int32_t hm = 0;
+        e = cudaMemcpyAsync(&hm, dM, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return e;
+        if (hm > M) hm = M;
+        gseq_out->assign(hm > 0 ? hm : 0, 0);
+        if (hm > 0)
+            e = cudaMemcpyAsync(gseq_out->data(), gseq, sizeof(int32_t) * (size_t)hm,
+                                cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return e;
+    }
     return cudaGetLastError();
 }
 

@@ -30,7 +30,8 @@ HGP_DEBUG_FORCE_GLOBAL = 4
 HGP_DEBUG_NO_BITMAP = 8
 HGP_DEBUG_FORCE_CLUSTER = 16
 (HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
- HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE, HGP_LEVEL_KEY) = range(9)
+ HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE, HGP_LEVEL_KEY,
+ HGP_LEVEL_GAIN_SEQ) = range(10)
 HGP_MLP_PARAMS = 641
 
 

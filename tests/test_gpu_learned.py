@@ -48,6 +48,10 @@ def compare_learned(g, omega, delta, model, passes=1, debug=0):
                     if a is not None:
                         assert np.array_equal(a, b), f"level {l} array {hw} differs"
                 assert tuple(G.level_array(l, H.HGP_LEVEL_REFINE).tolist()) == r.refine_stats(l)
+                a, b = G.level_array(l, H.HGP_LEVEL_GAIN_SEQ), r.array(l, oracle.A_GAIN_SEQ)
+                a = np.zeros(0, np.int64) if a is None else a
+                b = np.zeros(0, np.int64) if b is None else b
+                assert np.array_equal(a, b), f"level {l} in-sequence gains differ"
     assert np.array_equal(got.part_ids, want.part_ids)
     assert got.cost == want.cost and got.num_parts == want.num_parts
     assert np.array_equal(got.part_weight, want.part_weight)

@@ -53,6 +53,10 @@ def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False):
                             assert np.array_equal(a, b), f"level {l} array {hw} differs"
                     ref = G.level_array(l, H.HGP_LEVEL_REFINE)
                     assert tuple(ref.tolist()) == r.refine_stats(l), f"level {l} refinement"
+                    a, b = G.level_array(l, H.HGP_LEVEL_GAIN_SEQ), r.array(l, oracle.A_GAIN_SEQ)
+                    a = np.zeros(0, np.int64) if a is None else a
+                    b = np.zeros(0, np.int64) if b is None else b
+                    assert np.array_equal(a, b), f"level {l} in-sequence gains differ"
     assert np.array_equal(got.part_ids, want.part_ids)
     assert got.cost == want.cost
     assert got.num_parts == want.num_parts
