@@ -143,6 +143,67 @@ __device__ __forceinline__ uint32_t hash_node(uint32_t x) {
     return x;
 }
 
+// Candidates of one node are tested kLearnThreads at a time (one per thread)
+// and the valid ones compacted into shared memory, so the network runs on
+// full warps even where few node ids are neighbours (the cluster scorer's
+// slices of a large level, where about a quarter of the ids are).  cand(i, m, h, it)
+// loads entry i; the running best (comp, id) is kept per thread.
+struct LearnChunk {
+    int32_t lm[kLearnThreads], lh[kLearnThreads], li[kLearnThreads];
+    int32_t wc[kLearnWarps];
+};
+
+template <typename Load>
+__device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpParams &M, int32_t n,
+                                                int32_t cap, Load load, LearnChunk &ch,
+                                                unsigned long long &best_c, int32_t &best_m,
+                                                unsigned long long &bytes,
+                                                unsigned long long &evals) {
+    const int64_t in_n = a.noff[n + 1] - a.noff[n];
+    const int64_t wn = a.w[n];
+    for (int32_t base = 0; base < cap; base += kLearnThreads) {
+        const int32_t i = base + threadIdx.x;
+        int32_t m = 0, h = 0, it = 0;
+        bool ok = false;
+        if (i < cap) {
+            load(i, m, h, it);
+            ok = h != 0 && !(a.dead && a.dead[m]) && wn + a.w[m] <= a.omega &&
+                 in_n + (a.noff[m + 1] - a.noff[m]) - it <= a.delta;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, ok);
+        if (lane_id() == 0) ch.wc[warp_id()] = __popc(ball);
+        __syncthreads();
+        int32_t off = 0, total = 0;
+        for (int w = 0; w < kLearnWarps; ++w) {
+            const int32_t c = ch.wc[w];
+            off += w < warp_id() ? c : 0;
+            total += c;
+        }
+        if (ok) {
+            const int32_t q = off + __popc(ball & ((1u << lane_id()) - 1u));
+            ch.lm[q] = m;
+            ch.lh[q] = h;
+            ch.li[q] = it;
+        }
+        __syncthreads();
+        if ((int32_t)threadIdx.x < total) {
+            m = ch.lm[threadIdx.x];
+            h = ch.lh[threadIdx.x];
+            it = ch.li[threadIdx.x];
+            const int64_t in_m = a.noff[m + 1] - a.noff[m];
+            const int64_t uni = in_n + in_m - it;
+            float x[kMlpIn];
+            features(a, n, m, h, uni, in_n, in_m, x);
+            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
+            const unsigned long long c = composite(k, h);
+            if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
+            bytes += 20ull;
+            evals += 1ull;
+        }
+        __syncthreads();                      // the lists are reused by the next chunk
+    }
+}
+
 template <bool DENSE>
 __global__ void __launch_bounds__(kLearnThreads)
 k_score_learned(LearnedArgs a, MlpParams M) {
@@ -225,7 +286,8 @@ k_score_learned(LearnedArgs a, MlpParams M) {
             }
         }
         __syncthreads();
-        // ---- pass 2: the network on every valid neighbour ----
+        // ---- pass 2: the network on every valid neighbour (most of the ids
+        // tested here are neighbours, so the loop runs on nearly full warps) ----
         const int64_t in_n = a.noff[n + 1] - a.noff[n];
         const int64_t wn = a.w[n];
         unsigned long long best_c = 0ull;
@@ -284,6 +346,7 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
     __shared__ unsigned long long s_c[kLearnWarps];
     __shared__ int32_t s_i[kLearnWarps];
     __shared__ int32_t s_node;
+    __shared__ LearnChunk s_chunk;
     __shared__ unsigned long long s_xc;
     __shared__ int32_t s_xi;
     cg::cluster_group cl = cg::this_cluster();
@@ -342,27 +405,16 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
         }
         cl.sync();                                   // every slice complete
         // ---- pass 2: the network on this CTA's slice ----
-        const int64_t in_n = a.noff[n + 1] - a.noff[n];
-        const int64_t wn = a.w[n];
         unsigned long long best_c = 0ull;
         int32_t best_m = -1;
-        for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) {
-            const uint32_t v = cnt[i];
-            const int32_t h = (int32_t)(v >> 16), it = (int32_t)(v & 0xffffu), m = id0 + i;
-            if (h == 0) continue;
-            if (a.dead && a.dead[m]) continue;
-            if (wn + a.w[m] > a.omega) continue;
-            const int64_t in_m = a.noff[m + 1] - a.noff[m];
-            const int64_t uni = in_n + in_m - it;
-            if (uni > a.delta) continue;
-            float x[kMlpIn];
-            features(a, n, m, h, uni, in_n, in_m, x);
-            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
-            const unsigned long long cc = composite(k, h);
-            if (best_m < 0 || cc > best_c || (cc == best_c && m > best_m)) { best_c = cc; best_m = m; }
-            bytes += 20ull;
-            evals += 1ull;
-        }
+        eval_candidates(a, M, n, len,
+                        [&](int32_t i, int32_t &m, int32_t &h, int32_t &it) {
+                            const uint32_t v = cnt[i];
+                            m = id0 + i;
+                            h = (int32_t)(v >> 16);
+                            it = (int32_t)(v & 0xffffu);
+                        },
+                        s_chunk, best_c, best_m, bytes, evals);
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) { s_xc = best_c; s_xi = best_m; }
         for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) cnt[i] = 0u;
@@ -490,7 +542,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     const int32_t slice = (L.V + kLearnCluster - 1) / kLearnCluster;
     const size_t cl_smem = sizeof(uint32_t) * (size_t)slice;
     if (!(debug & HGP_DEBUG_FORCE_GLOBAL) && h_max[1] < 65536ull && L.max_in < 65536 &&
-        cl_smem + 4096 <= (size_t)max_smem) {
+        cl_smem + sizeof(LearnChunk) + 4096 <= (size_t)max_smem) {
         e = allow_dynamic_smem(k_score_learned_cluster);
         if (e) return e;
         cudaLaunchConfig_t cfg = {};
