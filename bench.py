@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -129,6 +130,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clocks_path(args, rank):
+    """Where the nvidia-smi samples of the timed region go (--clocks-dir)."""
+    d = args.clocks_dir or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, f"clocks_{args.workload}_rank{rank}.csv")
+
+
 def job_time_ms(local_ms: float, dist=None, device=None) -> float:
     """Timed region of the whole job: the maximum over ranks of each rank's
     summed step time (ranks run independent replicas)."""
@@ -213,7 +221,7 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    sampler = ClockSampler(f"/tmp/clocks_batch_rank{rank}.csv")
+    sampler = ClockSampler(clocks_path(args, rank))
     sampler.start()
     t = []
     for _ in range(args.steps):
@@ -401,8 +409,7 @@ def run_learned_large(args, rank, world):
     warm = 1 if args.warmup >= 1 else 0
     for _ in range(warm):
         step()
-    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    sampler = ClockSampler(clocks_path(args, rank))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -458,6 +465,8 @@ def main():
                          "hypergraphs through hgp_partition_batch; learned256k / learnedconv200k: "
                          "the learned order on the 262,144-node SNN / the 204,800-node conv-style "
                          "SNN (these print their own JSON line)")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the clock samples of the timed region (default: temp dir)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-order leg (training + timed learned partitions)")
     ap.add_argument("--save-model", default=None,
@@ -525,8 +534,7 @@ def main():
                           "launches": st["kernel_launches"] + st["create_launches"]}))
         return
 
-    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    sampler = ClockSampler(clocks_path(args, rank))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
