@@ -157,8 +157,8 @@ typedef struct {
  * Partition the handle's hypergraph under node bound `omega` (>= 1) and
  * inbound-hyperedge bound `delta` (>= 0).  Parts are the non-empty clusters
  * of the final partition, renumbered 0..num_parts-1 in the order of their
- * internal ids.  The result is a pure function of (graph, omega, delta,
- * refine_passes).
+ * internal ids.  The result is a pure function of (graph and its creation
+ * flags, omega, delta, refine_passes, max_levels, model).
  * Returns HGP_ERR_INFEASIBLE when some node alone has weight > omega or
  * |in(n)| > delta (then no partition exists), HGP_ERR_INVALID_ARG for bad
  * bounds/options/null part_ids.  Host outputs are complete on return; device
