@@ -143,26 +143,40 @@ __device__ __forceinline__ uint32_t hash_node(uint32_t x) {
     return x;
 }
 
-// Candidates of one node are tested kLearnThreads at a time (one per thread)
-// and the valid ones compacted into shared memory, so the network runs on
-// full warps even where few node ids are neighbours (the cluster scorer's
-// slices of a large level, where about a quarter of the ids are).  cand(i, m, h, it)
-// loads entry i; the running best (comp, id) is kept per thread.
-struct LearnChunk {
-    int32_t lm[kLearnThreads], lh[kLearnThreads], li[kLearnThreads];
-    int32_t wc[kLearnWarps];
+// Candidates of one node: each warp tests 32 ids at a time and queues the
+// valid ones in shared memory; whenever 32 are queued the warp evaluates the
+// network on all of them at once.  So the network runs on full warps even
+// where few ids are neighbours, with no CTA-wide barrier.  load(i, m, h, it)
+// reads entry i; the running best (comp, id) is kept per thread.
+struct LearnQueue {
+    int32_t m[kLearnWarps][64], h[kLearnWarps][64], it[kLearnWarps][64];
 };
 
 template <typename Load>
 __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpParams &M, int32_t n,
-                                                int32_t cap, Load load, LearnChunk &ch,
+                                                int32_t cap, Load load, LearnQueue &Q,
                                                 unsigned long long &best_c, int32_t &best_m,
                                                 unsigned long long &bytes,
                                                 unsigned long long &evals) {
+    const int w = warp_id(), lane = lane_id();
+    int32_t *qm = Q.m[w], *qh = Q.h[w], *qi = Q.it[w];
     const int64_t in_n = a.noff[n + 1] - a.noff[n];
     const int64_t wn = a.w[n];
-    for (int32_t base = 0; base < cap; base += kLearnThreads) {
-        const int32_t i = base + threadIdx.x;
+    auto evaluate = [&](int32_t slot) {
+        const int32_t m = qm[slot], h = qh[slot], it = qi[slot];
+        const int64_t in_m = a.noff[m + 1] - a.noff[m];
+        const int64_t uni = in_n + in_m - it;
+        float x[kMlpIn];
+        features(a, n, m, h, uni, in_n, in_m, x);
+        const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
+        const unsigned long long c = composite(k, h);
+        if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
+        bytes += 20ull;
+        evals += 1ull;
+    };
+    int32_t qn = 0;                                      // warp-uniform queue length (< 32 here)
+    for (int32_t base = w * 32; base < cap; base += kLearnThreads) {
+        const int32_t i = base + lane;
         int32_t m = 0, h = 0, it = 0;
         bool ok = false;
         if (i < cap) {
@@ -171,37 +185,28 @@ __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpP
                  in_n + (a.noff[m + 1] - a.noff[m]) - it <= a.delta;
         }
         const unsigned ball = __ballot_sync(0xffffffffu, ok);
-        if (lane_id() == 0) ch.wc[warp_id()] = __popc(ball);
-        __syncthreads();
-        int32_t off = 0, total = 0;
-        for (int w = 0; w < kLearnWarps; ++w) {
-            const int32_t c = ch.wc[w];
-            off += w < warp_id() ? c : 0;
-            total += c;
-        }
         if (ok) {
-            const int32_t q = off + __popc(ball & ((1u << lane_id()) - 1u));
-            ch.lm[q] = m;
-            ch.lh[q] = h;
-            ch.li[q] = it;
+            const int32_t pos = qn + __popc(ball & ((1u << lane) - 1u));
+            qm[pos] = m;
+            qh[pos] = h;
+            qi[pos] = it;
         }
-        __syncthreads();
-        if ((int32_t)threadIdx.x < total) {
-            m = ch.lm[threadIdx.x];
-            h = ch.lh[threadIdx.x];
-            it = ch.li[threadIdx.x];
-            const int64_t in_m = a.noff[m + 1] - a.noff[m];
-            const int64_t uni = in_n + in_m - it;
-            float x[kMlpIn];
-            features(a, n, m, h, uni, in_n, in_m, x);
-            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
-            const unsigned long long c = composite(k, h);
-            if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
-            bytes += 20ull;
-            evals += 1ull;
+        qn += __popc(ball);
+        __syncwarp();
+        if (qn >= 32) {
+            evaluate(lane);
+            __syncwarp();
+            if (lane < qn - 32) {
+                qm[lane] = qm[32 + lane];
+                qh[lane] = qh[32 + lane];
+                qi[lane] = qi[32 + lane];
+            }
+            __syncwarp();
+            qn -= 32;
         }
-        __syncthreads();                      // the lists are reused by the next chunk
     }
+    if (lane < qn) evaluate(lane);
+    __syncwarp();                                        // the queue is reused by the next node
 }
 
 template <bool DENSE>
@@ -213,6 +218,7 @@ k_score_learned(LearnedArgs a, MlpParams M) {
     __shared__ unsigned long long s_c[kLearnWarps];
     __shared__ int32_t s_i[kLearnWarps];
     __shared__ int32_t s_n, s_used;
+    __shared__ LearnQueue s_queue;
     // hash mode: the table is cleared once here, then only the slots a node
     // used (listed in gu) are visited and reset
     int32_t *gk = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
@@ -286,31 +292,16 @@ k_score_learned(LearnedArgs a, MlpParams M) {
             }
         }
         __syncthreads();
-        // ---- pass 2: the network on every valid neighbour (most of the ids
-        // tested here are neighbours, so the loop runs on nearly full warps) ----
-        const int64_t in_n = a.noff[n + 1] - a.noff[n];
-        const int64_t wn = a.w[n];
+        // ---- pass 2: the network on every valid neighbour ----
         unsigned long long best_c = 0ull;
         int32_t best_m = -1;
         const int32_t cap = DENSE ? a.V : s_used;
-        for (int32_t i = threadIdx.x; i < cap; i += kLearnThreads) {
-            int32_t m, h, it;
-            if (DENSE) { m = i; h = hist[i]; it = inter[i]; }
-            else { int32_t sl = gu[i]; m = gk[sl]; h = gv[sl]; it = gi[sl]; }
-            if (h == 0) continue;
-            if (a.dead && a.dead[m]) continue;
-            if (wn + a.w[m] > a.omega) continue;
-            const int64_t in_m = a.noff[m + 1] - a.noff[m];
-            const int64_t uni = in_n + in_m - it;
-            if (uni > a.delta) continue;
-            float x[kMlpIn];
-            features(a, n, m, h, uni, in_n, in_m, x);
-            const int32_t k = key_of(mlp_eval(M, x), M.key_bits);
-            const unsigned long long c = composite(k, h);
-            if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
-            bytes += 20ull;
-            evals += 1ull;
-        }
+        eval_candidates(a, M, n, cap,
+                        [&](int32_t i, int32_t &m, int32_t &h, int32_t &it) {
+                            if (DENSE) { m = i; h = hist[i]; it = inter[i]; }
+                            else { int32_t sl = gu[i]; m = gk[sl]; h = gv[sl]; it = gi[sl]; }
+                        },
+                        s_queue, best_c, best_m, bytes, evals);
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) {
             a.pair[n] = best_m;
@@ -346,7 +337,7 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
     __shared__ unsigned long long s_c[kLearnWarps];
     __shared__ int32_t s_i[kLearnWarps];
     __shared__ int32_t s_node;
-    __shared__ LearnChunk s_chunk;
+    __shared__ LearnQueue s_queue;
     __shared__ unsigned long long s_xc;
     __shared__ int32_t s_xi;
     cg::cluster_group cl = cg::this_cluster();
@@ -414,7 +405,7 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
                             h = (int32_t)(v >> 16);
                             it = (int32_t)(v & 0xffffu);
                         },
-                        s_chunk, best_c, best_m, bytes, evals);
+                        s_queue, best_c, best_m, bytes, evals);
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) { s_xc = best_c; s_xi = best_m; }
         for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) cnt[i] = 0u;
@@ -512,7 +503,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     if (e) return e;
     const int sms = num_sms();
     const size_t dense_smem = 2 * sizeof(int32_t) * (size_t)L.V;
-    if (dense_smem + 4096 <= (size_t)max_smem &&
+    if (dense_smem + sizeof(LearnQueue) + 4096 <= (size_t)max_smem &&
         !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER))) {
         e = allow_dynamic_smem(k_score_learned<true>);
         if (e) return e;
@@ -542,7 +533,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     const int32_t slice = (L.V + kLearnCluster - 1) / kLearnCluster;
     const size_t cl_smem = sizeof(uint32_t) * (size_t)slice;
     if (!(debug & HGP_DEBUG_FORCE_GLOBAL) && h_max[1] < 65536ull && L.max_in < 65536 &&
-        cl_smem + sizeof(LearnChunk) + 4096 <= (size_t)max_smem) {
+        cl_smem + sizeof(LearnQueue) + 4096 <= (size_t)max_smem) {
         e = allow_dynamic_smem(k_score_learned_cluster);
         if (e) return e;
         cudaLaunchConfig_t cfg = {};
