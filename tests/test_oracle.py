@@ -448,6 +448,24 @@ def test_fill_baseline_definition(seed, omega, delta):
         assert len(members) + 1 > omega or len(u | ins[nxt]) > delta
 
 
+def test_fill_baseline_weighted():
+    """Node weights count towards Omega: every part respects it and each next
+    part's first node would have broken a bound."""
+    g = synth.random_snn(250, 8, 9, size_max=12)
+    g.node_weights = np.random.default_rng(2).integers(1, 5, size=250).astype(np.int32)
+    omega, delta = 12, 50
+    ins = in_sets(g.num_nodes, g.offsets, g.pins)
+    with oracle.Run.from_graph(g) as r:
+        ids, k = r.fill_baseline(omega, delta)
+    st = part_stats(g.num_nodes, g.offsets, g.pins, ids, g.node_weights)
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    for p in range(k - 1):
+        members = np.nonzero(ids == p)[0]
+        nxt = members[-1] + 1
+        u = set().union(*(ins[n] for n in members))
+        assert int(g.node_weights[members].sum() + g.node_weights[nxt]) > omega or len(u | ins[nxt]) > delta
+
+
 def test_fill_baseline_closed_forms():
     g = synth.random_snn(100, 5, 1)
     with oracle.Run.from_graph(g) as r:
