@@ -3,6 +3,7 @@ run inside the test suite.  Calls only the CPU oracle and the seeded input
 generators; nothing here touches the CUDA library.
 
     python tests/golden/make_expected.py snn16k     # 16,384-node SNN, Omega 2^10, Delta 2^12
+    python tests/golden/make_expected.py batch64    # six members of the 64-instance batch
 
 Output: tests/golden/expected_<name>.txt with the Eq. (1) cost, the number of
 parts, the number of levels, the per-level node counts, and a SHA-256 of
@@ -32,7 +33,35 @@ def digest(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
+# members of synth.batch_instances(64, 0) small enough for the oracle (conv-style
+# and random, 2k-6k nodes), all at Omega 2^10, Delta 2^12
+BATCH_MEMBERS = (11, 3, 27, 6, 0, 42)
+
+
+def batch64():
+    inst = synth.batch_instances(64, 0)
+    path = os.path.join(ROOT, "tests", "golden", "expected_batch64.txt")
+    lines = ["# oracle results for members of the 64-instance batch (seed 0), omega=1024, delta=4096",
+             "# written by tests/golden/make_expected.py batch64",
+             "# member: cost num_parts num_levels sha_part_ids sha_part_stats"]
+    for i in BATCH_MEMBERS:
+        g = inst[i]
+        t = time.time()
+        with oracle.Run.from_graph(g) as r:
+            res = r.partition(1024, 4096)
+            nlev = r.num_levels
+        stats = np.stack([res.part_weight.astype(np.int64), res.part_inbound.astype(np.int64)], axis=1)
+        lines.append(f"{i}: {res.cost} {res.num_parts} {nlev} {digest(res.part_ids.astype('<i4'))} "
+                     f"{digest(stats.astype('<i8'))}  # {g.name}, {time.time() - t:.0f} s")
+        print(lines[-1], flush=True)
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print(path)
+
+
 def main(name: str):
+    if name == "batch64":
+        return batch64()
     make, omega, delta = WORKLOADS[name]
     g = make()
     t = time.time()

@@ -77,3 +77,52 @@ def test_batch_reports_per_instance_status():
         assert np.array_equal(keep[i], want.part_ids) and res[i].cost == want.cost
     for G in graphs:
         G.close()
+
+
+def _recount(g, ids):
+    """(cost, max part weight, max part inbound count), vectorised."""
+    off = g.offsets.astype(np.int64)
+    E = len(off) - 1
+    eid = np.repeat(np.arange(E, dtype=np.int64), np.diff(off))
+    part = ids[g.pins].astype(np.int64)
+    K = int(ids.max()) + 1
+    lam = np.bincount(np.unique(eid * K + part) // K, minlength=E)
+    first = np.zeros(len(g.pins), bool)
+    first[off[:-1]] = True
+    inb = np.bincount(np.unique(part[~first] * E + eid[~first]) // E, minlength=K)
+    return int((lam - 1).sum()), int(np.bincount(ids).max()), int(inb.max())
+
+
+@pytest.mark.slow
+def test_batch64_full_size():
+    """The 64-instance batch of the bench (150.8 M pins) in one
+    hgp_partition_batch call: six members against oracle results stored by
+    tests/golden/make_expected.py, every member recounted (cost, bounds)."""
+    import hashlib
+    import os
+    from conftest import ROOT
+    path = os.path.join(ROOT, "tests", "golden", "expected_batch64.txt")
+    if not os.path.exists(path):
+        pytest.skip("expected_batch64.txt not generated")
+    want = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = line.split(":", 1)
+            want[int(k)] = v.split()
+    inst = synth.batch_instances(64, 0)
+    graphs = [hgp.Graph.from_hypergraph(g) for g in inst]
+    try:
+        res = H.hgp_partition_batch(graphs, [1024] * 64, [4096] * 64)
+    finally:
+        for G in graphs:
+            G.close()
+    for i, (g, r) in enumerate(zip(inst, res)):
+        cost, wmax, inmax = _recount(g, r.part_ids)
+        assert cost == r.cost and wmax <= 1024 and inmax <= 4096, i
+        if i in want:
+            c, k, nlev, sha_ids, sha_stats = want[i]
+            assert r.cost == int(c) and r.num_parts == int(k) and r.num_levels == int(nlev), i
+            assert hashlib.sha256(r.part_ids.astype("<i4").tobytes()).hexdigest() == sha_ids, i
+            st = np.stack([r.part_weight.astype(np.int64), r.part_inbound.astype(np.int64)], axis=1)
+            assert hashlib.sha256(st.astype("<i8").tobytes()).hexdigest() == sha_stats, i
