@@ -49,8 +49,9 @@ SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same gener
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel
-# (profiles/k_score_snn16k_level200.md: mean over the 435 launches of one
-# step), valid only while the kernel's sources are the ones captured.
+# (dram__bytes_read.sum + dram__bytes_write.sum of all 435 launches of one
+# step of this workload, averaged), valid only while the kernel's sources are
+# the ones captured.
 MEASURED_TRAFFIC = {
     "k_score": (13478669.5, {
         "paper_2604_14411_gb300/csrc/k_score.cuh":
