@@ -427,8 +427,15 @@ def train_model(graphs, omega, delta, seed=0, per_node=16, steps=2000, batch=409
     perm = torch.randperm(x.shape[0], generator=gen).to(x.device)
     x = x[perm].contiguous()
     y = y[perm].contiguous()
-    params = (np.zeros(HGP_MLP_PARAMS, np.float32) if init_params is None
-              else np.array(init_params, dtype=np.float32))
+    if init_params is None:
+        # seeded start: W1 uniform in +-1/sqrt(8), W2 uniform in +-1/8, biases 0
+        # (an all-zero start never breaks the hidden units' symmetry)
+        rng = np.random.default_rng(seed)
+        params = np.zeros(HGP_MLP_PARAMS, np.float32)
+        params[:512] = rng.uniform(-1, 1, size=512) / np.sqrt(8.0)
+        params[576:640] = rng.uniform(-1, 1, size=64) / 8.0
+    else:
+        params = np.array(init_params, dtype=np.float32)
     adam = np.zeros(2 * HGP_MLP_PARAMS, np.float32)
     torch.cuda.synchronize()
     losses = hgp_train_mlp(x, y, params, adam, steps, batch, lr, stream=stream)

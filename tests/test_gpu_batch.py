@@ -96,8 +96,9 @@ def _recount(g, ids):
 @pytest.mark.slow
 def test_batch64_full_size():
     """The 64-instance batch of the bench (150.8 M pins) in one
-    hgp_partition_batch call: six members against oracle results stored by
-    tests/golden/make_expected.py, every member recounted (cost, bounds)."""
+    hgp_partition_batch call: the members whose oracle results
+    tests/golden/make_expected.py stored (every conv-style member and three
+    random ones) bit-exact, every member recounted (cost, bounds)."""
     import hashlib
     import os
     from conftest import ROOT
