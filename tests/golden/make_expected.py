@@ -3,7 +3,7 @@ run inside the test suite.  Calls only the CPU oracle and the seeded input
 generators; nothing here touches the CUDA library.
 
     python tests/golden/make_expected.py snn16k     # 16,384-node SNN, Omega 2^10, Delta 2^12
-    python tests/golden/make_expected.py batch64    # 35 members of the 64-instance batch
+    python tests/golden/make_expected.py batch64    # 39 members of the 64-instance batch
 
 Output: tests/golden/expected_<name>.txt with the Eq. (1) cost, the number of
 parts, the number of levels, the per-level node counts, and a SHA-256 of
@@ -35,8 +35,8 @@ def digest(a: np.ndarray) -> str:
 
 # members of synth.batch_instances(64, 0) the oracle finishes in minutes, all
 # at Omega 2^10, Delta 2^12: every conv-style member (odd index, 2k-59k
-# nodes, up to 11.9 M pins) and three random ones (3k-5k nodes)
-BATCH_MEMBERS = tuple(range(1, 64, 2)) + (6, 0, 42)
+# nodes, up to 11.9 M pins) and seven random ones (3k-5k nodes)
+BATCH_MEMBERS = tuple(range(1, 64, 2)) + (6, 0, 42, 32, 40, 24, 48)
 
 
 def batch64():
