@@ -8,17 +8,25 @@ Eq. (2) scoring with deferred checks, matching, contraction; every
 refinement level: Eq. (3) moves, in-sequence gains, prefix validity;
 projection; output) + hgp_destroy.
 
-value = level-0 pins / step time (pins/s), whole job over all ranks.
+value = level-0 pins / step time (pins/s), whole job over all ranks, from
+        steps with no instrumentation; a few separate steps with CUDA events
+        around every phase give the kernel split and the rooflines.
 e2e   = the same through the C ABI with pinned HOST input and output
         buffers, the copies inside the timed region.
 The L2 (129 MB) is flushed between timed steps (the inputs are 8.4 MB).
+The same line also reports the learned candidate order on this workload
+(model trained untimed on seeded 16k-64k-node graphs), the constraint-only
+fill as a quality floor, and whole plain and learned partitions of the
+262,144-node SNN (67 M pins) with their cost and time ratio.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-With --impl reference the CPU oracle (the plain single-threaded C
-restatement of the method used for parity) is timed on the host cores on a
-bounded sample of the workload family.  Multi-GPU: independent replicas
-(the method does not shard), one per rank under torchrun.
+cpu_baseline and --impl reference time the CPU oracle (the plain
+single-threaded C restatement of the method used for parity) on the host
+cores on a bounded sample of this same workload: the method cut after its
+first coarsening level (the GPU's time on the same cut is reported beside
+it).  Multi-GPU: independent replicas (the method does not shard), one per
+rank under torchrun.
 """
 from __future__ import annotations
 
@@ -40,12 +48,18 @@ sys.path.insert(0, ROOT)
 METRIC = "coarsening pins/s and partition wall-time at equal λ−1 cost, plain vs learned"
 OMEGA, DELTA = 1 << 10, 1 << 12
 WORKLOAD = "random SNN hypergraph, 16,384 nodes, one hyperedge per node of 128 pins (src + 127 distinct targets), 2,097,152 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0"
-LEARN_TRAIN_GRAPHS, LEARN_PER_NODE, LEARN_STEPS, LEARN_BATCH, LEARN_LR, LEARN_KEY_BITS = \
-    4, 16, 2000, 4096, 3e-3, 6
+# training set of the learned order: random SNN graphs of 16k, 32k and 64k
+# nodes (cycling), hyperedges of 128..256 pins, seeds 100..115
+LEARN_TRAIN_GRAPHS, LEARN_TRAIN_SIZES = 16, (16384, 32768, 65536)
+LEARN_PER_NODE, LEARN_STEPS, LEARN_BATCH, LEARN_LR, LEARN_KEY_BITS = 4, 2000, 4096, 3e-3, 6
 LEARN_SM_GHZ = 2.07          # maximum SM clock of the GB300
-SAMPLE_DESC = ("full oracle partition of the 2,048-node member of the same generator family "
-               "(32 pins per hyperedge, 65,536 pins, Omega=128, Delta=512, seed 0); the 16k-node "
-               "workload needs well over 10 minutes of oracle time on one core")
+INSTRUMENTED_STEPS = 2       # separate steps with phase events, for the kernel split
+CUT_LEVELS = 1               # the CPU baseline's bounded prefix of the method
+SAMPLE_DESC = ("the same workload (16k SNN, Omega=2^10, Delta=2^12) through the method's first "
+               f"{CUT_LEVELS} coarsening level(s): incidence build, Eq. 2 scoring with the "
+               "Omega/Delta checks, matching, then refinement of that level from the matched "
+               "clusters (hgp_options.max_levels / the oracle's cut; the whole method takes "
+               "435 levels and ~2,100 s of oracle time on one core)")
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel
@@ -154,16 +168,21 @@ def job_value(units_per_step: int, steps: int, world: int, job_ms: float) -> flo
     return units_per_step * steps * world / (job_ms / 1000.0)
 
 
+def _oracle_cut_step(g):
+    """One bounded sample on the CPU oracle: build + the method cut after
+    CUT_LEVELS levels, as one GPU step builds and partitions."""
+    import oracle
+    t = time.perf_counter()
+    with oracle.Run.from_graph(g) as r:
+        r.partition(OMEGA, DELTA, 1, CUT_LEVELS)
+    return time.perf_counter() - t
+
+
 def oracle_sample(steps=1):
     """Times the CPU oracle on the bounded sample; returns (pins/s, seconds)."""
-    import oracle
     import synth
-    g = synth.snn_2k(0)
-    ts = []
-    for _ in range(steps):
-        t = time.perf_counter()
-        oracle.partition(g, 128, 512)
-        ts.append(time.perf_counter() - t)
+    g = synth.snn_16k(0)
+    ts = [_oracle_cut_step(g) for _ in range(steps)]
     return g.num_pins / statistics.median(ts), ts
 
 
@@ -171,23 +190,19 @@ def run_reference(args, rank, world):
     """CPU oracle arm: rank 0 only, K timed steps of the bounded sample."""
     if rank != 0:
         return
-    import oracle
     import synth
-    g = synth.snn_2k(0)
+    g = synth.snn_16k(0)
     for _ in range(args.warmup):
-        oracle.partition(g, 128, 512)
-    ts = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.partition(g, 128, 512)
-        ts.append(time.perf_counter() - t)
+        _oracle_cut_step(g)
+    ts = [_oracle_cut_step(g) for _ in range(args.steps)]
     tot = sum(ts)
     value = g.num_pins * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": SAMPLE_DESC},
+            "config": {"workload": WORKLOAD, "omega": OMEGA, "delta": DELTA, "pins": 2097152,
+                       "sample": SAMPLE_DESC},
             "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
                              "sample": SAMPLE_DESC},
             "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -240,12 +255,7 @@ def run_batch(args, rank, world):
     learned = None
     if not args.no_learned:
         # the same batch with the learned order (model trained untimed on 16k-node graphs)
-        t0 = time.perf_counter()
-        model, _ = H.train_model(synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,)),
-                                 OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE, steps=LEARN_STEPS,
-                                 batch=LEARN_BATCH, lr=LEARN_LR, key_bits=LEARN_KEY_BITS,
-                                 init_params=synth.initial_params(0))
-        train_s = time.perf_counter() - t0
+        model, _, train_s, _ = train_learned_model(H, None)
         H.hgp_partition_batch(graphs, om, de, model=model)
         torch.cuda.synchronize()
         lt = []
@@ -296,34 +306,34 @@ def recount(g, ids, omega, delta):
     return cost, bool(weight.max() <= omega and inbound.max() <= delta)
 
 
-def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
-    """Learned candidate order: train on seeded graphs of the same family
-    (untimed), then time partitions of the workload with the trained model."""
-    import torch
+def train_learned_model(H, stream):
+    """The learned order's model, trained (untimed) on the seeded training set."""
     import synth
     t0 = time.perf_counter()
-    train = synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,))
+    train = synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=LEARN_TRAIN_SIZES)
     model, losses = H.train_model(train, OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE,
                                   steps=LEARN_STEPS, batch=LEARN_BATCH, lr=LEARN_LR,
                                   key_bits=LEARN_KEY_BITS, init_params=synth.initial_params(0),
                                   stream=stream)
-    train_s = time.perf_counter() - t0
+    pairs = LEARN_PER_NODE * sum(t.num_nodes for t in train)
+    return model, losses, time.perf_counter() - t0, pairs
+
+
+def learned_leg(args, timed, g, d_ids, plain_cost, plain_ms, H, stream):
+    """Learned candidate order: train on seeded graphs of the same family
+    (untimed), then time partitions of the workload with the trained model.
+    Returns (report, model)."""
+    import torch
+    model, losses, train_s, pairs = train_learned_model(H, stream)
     if args.save_model:
         np.savez(args.save_model, w1=model.w1, b1=model.b1, w2=model.w2, b2=model.b2,
                  key_bits=model.key_bits)
-    step(model=model)
+    timed(model=model)
     torch.cuda.synchronize()
-    times, stats, res = [], [], None
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.fill_(1)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        res, st = step(H.HGP_DEBUG_TIMING, model=model)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-        stats.append(st)
+    runs = [timed(model=model) for _ in range(max(1, min(args.steps, 3)))]
+    times = [r[0] for r in runs]
+    res = runs[-1][1]
+    stats = [timed(H.HGP_DEBUG_TIMING, model=model)[2] for _ in range(INSTRUMENTED_STEPS)]
     ms = statistics.median(times)
     ids = d_ids.cpu().numpy()
     cost, feasible = recount(g, ids, OMEGA, DELTA)
@@ -335,12 +345,14 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
     peak_tflops = 152 * 128 * 2 * LEARN_SM_GHZ / 1000.0
     achieved = flops / (sc_ms / 1000.0) / 1e12 if sc_ms > 0 else 0.0
     return {"model": f"8-64-1 MLP, bfloat16 weights, key_bits {LEARN_KEY_BITS}",
-            "training": {"graphs": f"{LEARN_TRAIN_GRAPHS} random SNN hypergraphs, 16,384 nodes, "
-                                   "hyperedge size 128..256, seeds 100..", "labels": "co-location in "
-                                   "the plain partition", "pairs": LEARN_PER_NODE * 16384 * LEARN_TRAIN_GRAPHS,
+            "training": {"graphs": f"{LEARN_TRAIN_GRAPHS} random SNN hypergraphs of "
+                                   f"{'/'.join(str(x) for x in LEARN_TRAIN_SIZES)} nodes (cycling), "
+                                   f"hyperedge size 128..256, seeds 100..{99 + LEARN_TRAIN_GRAPHS}",
+                         "labels": "co-location in the plain partition", "pairs": pairs,
                          "steps": LEARN_STEPS, "batch": LEARN_BATCH, "seconds": train_s,
                          "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean())},
             "ms_per_step": ms, "pins_per_s": g.num_pins / (ms / 1000.0),
+            "timing": "uninstrumented steps; split and roofline from separate instrumented steps",
             "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
             "coarsening_pins_per_s": g.num_pins / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
             "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
@@ -354,18 +366,18 @@ def learned_leg(args, step, flush, stream, g, d_ids, plain_cost, plain_ms, H):
                          "evals_per_step": evals / len(stats),
                          "score_ms_per_step": sc_ms / len(stats),
                          "hbm_achieved_gbs": (sum(s["score_bytes"] for s in stats) / 1e9) / (sc_ms / 1000.0)
-                         if sc_ms > 0 else 0.0}}
+                         if sc_ms > 0 else 0.0}}, model
 
 
 LEARNED_LARGE = {
     "learned256k": ("learned candidate order on a random SNN hypergraph, 262,144 nodes, one "
                     "hyperedge per node of 256 pins, 67,108,864 pins, int32 CSR, Omega=2^10, "
-                    "Delta=2^12, seed 0; model trained on 4 seeded 16,384-node graphs",
+                    "Delta=2^12, seed 0; model trained on 16 seeded 16k-64k-node graphs",
                     "snn_256k", 1 << 10, 1 << 12),
     "learnedconv200k": ("learned candidate order on a layered conv-style SNN hypergraph, 8 layers x "
                         "16x16 x 100 channels (204,800 nodes), 3x3 windows on 88..100 channels, "
-                        "~1.4e8 pins, int32 CSR, Omega=2^12, Delta=2^16, seed 0; model trained on 4 "
-                        "seeded 16,384-node random SNN graphs", "conv_200k", 1 << 12, 1 << 16),
+                        "~1.4e8 pins, int32 CSR, Omega=2^12, Delta=2^16, seed 0; model trained on 16 "
+                        "seeded 16k-64k-node random SNN graphs", "conv_200k", 1 << 12, 1 << 16),
 }
 
 
@@ -384,12 +396,7 @@ def run_learned_large(args, rank, world):
     H.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    model, losses = H.train_model(synth.training_graphs(LEARN_TRAIN_GRAPHS, 100, sizes=(16384,)),
-                                  OMEGA, DELTA, seed=0, per_node=LEARN_PER_NODE, steps=LEARN_STEPS,
-                                  batch=LEARN_BATCH, lr=LEARN_LR, key_bits=LEARN_KEY_BITS,
-                                  init_params=synth.initial_params(0), stream=stream)
-    train_s = time.perf_counter() - t0
+    model, losses, train_s, _ = train_learned_model(H, stream)
     desc, make, omega, delta = LEARNED_LARGE[args.workload]
     g = getattr(synth, make)(0)
     N, P = g.num_nodes, g.num_pins
@@ -470,6 +477,8 @@ def main():
                     help="directory for the clock samples of the timed region (default: temp dir)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-order leg (training + timed learned partitions)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the whole plain and learned partitions of the 262,144-node SNN")
     ap.add_argument("--save-model", default=None,
                     help="write the learned leg's trained model to this .npz file")
     ap.add_argument("--learned-model", default=None,
@@ -512,14 +521,25 @@ def main():
     d_pin = torch.empty(N, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
-    def step(debug=0, model=None):
+    def step(debug=0, model=None, max_levels=0):
         h = H.hgp_create(N, d_off, d_pins, stream=stream)
         try:
-            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug, 0, model)
+            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug, max_levels, model)
             st = H.hgp_get_stats(h)
         finally:
             H.hgp_destroy(h)
         return res, st
+
+    def timed(debug=0, model=None, max_levels=0):
+        """One step between CUDA events on the library's stream, L2 flushed first."""
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, st = step(debug, model, max_levels)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), res, st
 
     for _ in range(args.warmup):
         step()
@@ -535,6 +555,7 @@ def main():
                           "launches": st["kernel_launches"] + st["create_launches"]}))
         return
 
+    # ---- timed region: K whole steps, no instrumentation inside ----
     sampler = ClockSampler(clocks_path(args, rank))
     if dist:
         dist.barrier()
@@ -542,14 +563,8 @@ def main():
     sampler.start()
     times, stats, res = [], [], None
     for _ in range(args.steps):
-        flush.fill_(1)                               # L2 flush, outside the timed region
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        res, st = step(H.HGP_DEBUG_TIMING)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
+        ms, res, st = timed()
+        times.append(ms)
         stats.append(st)
     torch.cuda.synchronize()
     clocks = sampler.stop(local)
@@ -558,6 +573,10 @@ def main():
     t_total = job_time_ms(sum(times), dist, dev)
     ms_per_step = t_total / args.steps
     value = job_value(P, args.steps, world, t_total)
+
+    # ---- per-kernel split: separate steps with CUDA events around every phase ----
+    inst = [timed(H.HGP_DEBUG_TIMING) for _ in range(INSTRUMENTED_STEPS)]
+    istats = [x[2] for x in inst]
 
     # end to end through the C ABI with pinned host buffers
     h_off = torch.from_numpy(g.offsets.copy()).pin_memory()
@@ -582,9 +601,9 @@ def main():
     h2d = g.offsets.nbytes + g.pins.nbytes
     d2h = h_ids.numel() * 4 + nparts * 8 + nparts * 4 + 8 + 4
 
-    learned = None
+    learned, model = None, None
     if not args.no_learned:
-        learned = learned_leg(args, step, flush, stream, g, d_ids, res[0], statistics.median(times), H)
+        learned, model = learned_leg(args, timed, g, d_ids, res[0], statistics.median(times), H, stream)
     # quality floor: the constraint-only comparison (parts filled in node-id order)
     with H.Graph(N, d_off, d_pins, stream=stream) as G:
         fill = G.fill_baseline(OMEGA, DELTA)
@@ -593,21 +612,31 @@ def main():
     if learned is not None:
         quality["learned_cost_vs_fill"] = learned["cost"] / fill.cost
 
-    st = stats[-1]
+    # the CPU baseline's sample on the GPU: the same cut prefix of the method
+    cut_ms = statistics.median(timed(max_levels=CUT_LEVELS)[0] for _ in range(5))
+
+    st = istats[-1]
     peak, peak_kind = load_peaks()
-    # roofline of the kernel with the largest summed device time in the timed steps
+    # roofline of the kernel with the largest summed device time in the instrumented steps
     kern = {
         "k_score": ("Eq. 2 scoring with deferred Omega/Delta checks",
-                    sum(s["ms_score"] for s in stats), sum(s["score_launches"] for s in stats),
-                    sum(s["score_bytes"] for s in stats)),
+                    sum(s["ms_score"] for s in istats), sum(s["score_launches"] for s in istats),
+                    sum(s["score_bytes"] for s in istats)),
         "k_propose": ("Eq. 3 in-isolation move proposals",
-                      sum(s["ms_propose"] for s in stats), sum(s["propose_launches"] for s in stats),
-                      sum(s["propose_bytes"] for s in stats)),
+                      sum(s["ms_propose"] for s in istats), sum(s["propose_launches"] for s in istats),
+                      sum(s["propose_bytes"] for s in istats)),
     }
     top = max(kern, key=lambda k: kern[k][1])
     desc, ms_k, n_k, bytes_k = kern[top]
     achieved = (bytes_k / 1e9) / (ms_k / 1000.0) if ms_k > 0 else 0.0
-    launches = int(st["kernel_launches"] + st["create_launches"])
+    launches = int(stats[-1]["kernel_launches"] + stats[-1]["create_launches"])
+    inst_ms = sum(x[0] for x in inst)
+
+    large = None
+    if not args.no_large:
+        del flush
+        torch.cuda.empty_cache()
+        large = large_leg(model, stream, H, peak)
 
     if rank == 0:
         line = {
@@ -619,11 +648,14 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "partition_ms": statistics.median(s["ms_partition"] for s in stats),
-            "coarsen_ms": statistics.median(s["ms_coarsen"] for s in stats),
-            "coarsening_pins_per_s": P / (statistics.median(s["ms_coarsen"] for s in stats) / 1000.0),
-            "refine_ms": statistics.median(s["ms_refine"] for s in stats),
-            "levels": st["num_levels"], "cost": res[0], "num_parts": res[1],
+            "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
             "gpu_launches": launches * args.steps,
+            "instrumented": {"steps": len(inst), "ms_per_step": inst_ms / len(inst),
+                             "note": "separate steps with CUDA events around every phase; the "
+                                     "split and the roofline below come from these"},
+            "coarsen_ms": statistics.median(s["ms_coarsen"] for s in istats),
+            "coarsening_pins_per_s": P / (statistics.median(s["ms_coarsen"] for s in istats) / 1000.0),
+            "refine_ms": statistics.median(s["ms_refine"] for s in istats),
             "e2e": {"value": e2e_value, "unit": "pins/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": {"kernel": f"{top} ({desc})", "bound": "hbm",
@@ -632,22 +664,88 @@ def main():
                          "peak_kind": f"{peak_kind} (hbm copy)",
                          "launches": int(n_k), "avg_launch_us": 1000.0 * ms_k / max(n_k, 1),
                          "bytes_per_launch": bytes_k / max(n_k, 1),
-                         "share_of_step": ms_k / sum(times)},
-            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kern.items()},
+                         "share_of_step": ms_k / inst_ms},
+            "contraction_roofline": contraction_roofline(istats, peak, peak_kind, "16k SNN, all levels"),
+            "kernel_ms_per_step": {k: v[1] / len(istats) for k, v in kern.items()},
             "clocks": clocks,
         }
         if learned is not None:
             line["learned"] = learned
         line["quality"] = quality
+        if large is not None:
+            line["snn256k"] = large
         if not args.no_cpu_baseline:
             v, ts = oracle_sample(steps=3)
+            gpu_cut = P / (cut_ms / 1000.0)
             line["cpu_baseline"] = {"value": v, "unit": "pins/s", "cores": 1, "kind": "oracle",
-                                    "sample": SAMPLE_DESC + f"; median of {len(ts)} runs"}
+                                    "sample": SAMPLE_DESC + f"; median of {len(ts)} runs",
+                                    "gpu_same_sample": {"value": gpu_cut, "unit": "pins/s",
+                                                        "ms": cut_ms, "ratio_vs_oracle": gpu_cut / v}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
+
+def contraction_roofline(stats, peak, peak_kind, where):
+    """Contraction kernels (count and write phases, without the host read in
+    between) against the HBM copy peak, from HGP_DEBUG_TIMING steps."""
+    ms = sum(s["ms_contract_kernels"] for s in stats)
+    by = sum(s["contract_bytes"] for s in stats)
+    ach = (by / 1e9) / (ms / 1000.0) if ms > 0 else 0.0
+    return {"kernels": "k_coarse_nodes, k_carry, k_union_count, k_union_merged, k_coarse_pins, "
+                       "k_union_copy, k_coarse_src + offset scans", "where": where, "bound": "hbm",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": f"{peak_kind} (hbm copy)", "ms": ms / len(stats),
+            "bytes": by / len(stats), "traffic": None}
+
+
+def large_leg(model, stream, H, peak):
+    """Whole partitions of the 262,144-node SNN (67 M pins): the plain order
+    and the learned one with the model trained above, each once, L2 flushed,
+    with phase events on (for the contraction roofline at these sizes)."""
+    import torch
+    import synth
+    g = synth.snn_256k(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_off = torch.from_numpy(g.offsets.copy()).to(dev)
+    d_pins = torch.from_numpy(g.pins.copy()).to(dev)
+    d_ids = torch.empty(g.num_nodes, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {"workload": "random SNN hypergraph, 262,144 nodes, one hyperedge per node of 256 pins, "
+                       "67,108,864 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0",
+           "timing": "one whole create + partition + destroy each, CUDA events on the library's "
+                     "stream, L2 flushed before, phase events on"}
+    legs = [("plain", None)] + ([("learned", model)] if model is not None else [])
+    for name, m in legs:
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        alloc = H.TorchAllocator()
+        a.record(stream)
+        h = H.hgp_create(g.num_nodes, d_off, d_pins, stream=stream, allocator=alloc)
+        try:
+            res = H.hgp_partition(h, 1 << 10, 1 << 12, d_ids, None, None, 1, H.HGP_DEBUG_TIMING, 0, m)
+            st = H.hgp_get_stats(h)
+        finally:
+            H.hgp_destroy(h)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        cost, feas = recount(g, d_ids.cpu().numpy(), 1 << 10, 1 << 12)
+        out[name] = {"ms": ms, "pins_per_s": g.num_pins / (ms / 1000.0), "levels": res[2],
+                     "cost": res[0], "num_parts": res[1], "cost_recounted": cost, "feasible": feas,
+                     "coarsen_ms": st["ms_coarsen"], "refine_ms": st["ms_refine"],
+                     "score_ms": st["ms_score"], "peak_device_gb": alloc.peak_bytes / 1e9}
+        if name == "plain":
+            out["contraction_roofline"] = contraction_roofline([st], peak, load_peaks()[1],
+                                                               "262k SNN, all 201 levels")
+    if "learned" in out:
+        out["learned"]["cost_ratio_vs_plain"] = out["learned"]["cost"] / out["plain"]["cost"]
+        out["learned"]["time_ratio_vs_plain"] = out["learned"]["ms"] / out["plain"]["ms"]
+    del d_off, d_pins, d_ids, flush
+    torch.cuda.empty_cache()
+    return out
 
 if __name__ == "__main__":
     main()

@@ -55,6 +55,9 @@ typedef enum {
 #define HGP_DELTA_INCIDENT 4u  /* hgp_create: Delta bounds the distinct hyperedges incident to a part
                                   (in(n) = I(n)) instead of the inbound ones; the paper notes the
                                   generalisation in Sec. II-A */
+#define HGP_DELTA_OUTBOUND 8u  /* hgp_create: Delta bounds the distinct hyperedges whose source lies
+                                  in the part (in(n) = {e : src(e) = n}), the other direction of the
+                                  same generalisation; not together with HGP_DELTA_INCIDENT */
 
 /* hgp_result.out_flags */
 #define HGP_OUTPUT_DEVICE 1u   /* part_ids/part_weight/part_inbound are device pointers */
@@ -68,8 +71,47 @@ typedef enum {
                                       of the shared-memory bitmap */
 #define HGP_DEBUG_FORCE_CLUSTER 16u /* test knob: score every level with the 8-CTA cluster
                                        kernel (distributed shared-memory histogram) */
+#define HGP_DEBUG_SMALL_TABLE 32u  /* test knob, with HGP_DEBUG_FORCE_GLOBAL: give the scoring
+                                      kernel's per-CTA hash tables 64 slots, so a node with more
+                                      distinct neighbours exhausts its bounded probe loop and the
+                                      call returns HGP_ERR_DEVICE_LIMIT */
+#define HGP_DEBUG_REBUILD_INC 64u  /* test knob: keep no coarse level's I(n) until refinement;
+                                      rebuild each from the level's pins when refinement reaches
+                                      it (the path levels beyond the memory budget take) */
 
 typedef struct hgp_graph hgp_graph;
+
+/*
+ * Device memory source of a handle (optional).  Every device buffer the
+ * library uses for a handle -- the level-0 structure held by the handle, each
+ * coarsening level kept until refinement reaches it, and the temporaries of a
+ * call -- comes from alloc() in chunks (64 MiB or larger for levels and
+ * temporaries, exact sizes for the handle's own arrays) and goes back through
+ * free() with the same size.
+ *   alloc(ctx, bytes, stream)      returns `bytes` of device memory on the
+ *                                  current device, 256-byte aligned, usable in
+ *                                  stream order on `stream`; NULL on failure
+ *                                  (the call then returns HGP_ERR_OOM after
+ *                                  returning every chunk it already holds)
+ *   free(ctx, ptr, bytes, stream)  the library has enqueued every use of ptr
+ *                                  on `stream` before this call; the memory
+ *                                  may be reused by work ordered after it on
+ *                                  that stream
+ *   ctx                            passed back unchanged
+ * `stream` is the handle's stream, or the per-instance stream that
+ * hgp_partition_batch creates (destroyed, after a synchronise, when the call
+ * returns).  The callbacks may be called from hgp_partition_batch's worker
+ * threads concurrently.  The struct is copied by hgp_create; ctx and the
+ * functions must stay valid until hgp_destroy.  A NULL allocator means
+ * cudaMallocAsync / cudaFreeAsync on the same streams.  (A host program that
+ * already owns a caching allocator, such as PyTorch's, passes it here so that
+ * the library draws from the same pool.)
+ */
+typedef struct {
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+    void *ctx;
+} hgp_allocator;
 
 /*
  * Build a hypergraph handle (the level-0 incidence structure of Sec. II-C:
@@ -85,9 +127,13 @@ typedef struct hgp_graph hgp_graph;
  *                 their sum must be < 2^31
  *   edge_weights  [num_edges] int32 >= 1, or NULL for unit weights (omega);
  *                 their sum must be < 2^31
- *   flags         HGP_INPUT_DEVICE: the four arrays are device memory;
- *                 HGP_DELTA_INCIDENT: Delta counts incident, not inbound, hyperedges
- *                 readable on `stream`; otherwise host memory
+ *   flags         HGP_INPUT_DEVICE: the four arrays are device memory
+ *                 readable on `stream` (otherwise host memory);
+ *                 HGP_DELTA_INCIDENT: Delta counts incident, not inbound, hyperedges;
+ *                 HGP_DELTA_OUTBOUND: Delta counts outbound hyperedges (sourced in the
+ *                 part); hgp_result.part_inbound then holds that count
+ *   alloc         device memory source for everything the handle and its calls
+ *                 use (see hgp_allocator), or NULL for cudaMallocAsync
  *   stream        cudaStream_t to run on (NULL = default stream)
  *   out           receives the handle
  * Ownership: inputs are copied; the caller may free them once the call has
@@ -98,7 +144,8 @@ typedef struct hgp_graph hgp_graph;
 int hgp_create(int32_t num_nodes, int32_t num_edges,
                const int32_t *offsets, const int32_t *pins,
                const int32_t *node_weights, const int32_t *edge_weights,
-               uint32_t flags, void *stream, hgp_graph **out);
+               uint32_t flags, const hgp_allocator *alloc, void *stream,
+               hgp_graph **out);
 
 /*
  * Learned candidate order (an extension; the paper has no counterpart).
@@ -198,7 +245,9 @@ typedef struct {
     double ms_contract;        /* contraction */
     int64_t score_launches;
     int64_t score_bytes;       /* algorithmic bytes of all scoring launches */
-    int64_t contract_bytes;    /* algorithmic bytes of all contractions */
+    int64_t contract_bytes;    /* HGP_DEBUG_TIMING: algorithmic bytes of all contractions
+                                  (4 B per pin read, gathered and written; 4 B per I and in
+                                  entry read and written; 12 B per hyperedge and node) */
     int64_t pins_total;        /* sum over built levels of the pin count */
     int64_t kernel_launches;   /* kernels launched by the last hgp_partition */
     int64_t moves_applied;     /* refinement moves applied, all levels */
@@ -208,6 +257,8 @@ typedef struct {
     int64_t propose_bytes;     /* algorithmic bytes of all proposal launches */
     int64_t learned_evals;     /* HGP_DEBUG_TIMING, learned order: network evaluations (each
                                   8 lg1p features + 576 FMA + 64 ReLU) over all levels */
+    double ms_contract_kernels; /* HGP_DEBUG_TIMING: device time of the contraction kernels
+                                   (count and write phases, without the host read between) */
 } hgp_stats;
 
 /* Statistics of the handle's last hgp_partition (and hgp_create). */

@@ -58,8 +58,11 @@ def _load():
             vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
             lib.orun_create.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
             lib.orun_create_incident.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+            lib.orun_create_outbound.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
             lib.orun_destroy.argtypes = [vp]
             lib.orun_partition.argtypes = [vp, i64, i64, i32]
+            lib.orun_partition_cut.argtypes = [vp, i64, i64, i32, i32]
+            lib.orun_partition_ex.argtypes = [vp, i64, i64, i32, i32, i32]
             for name, rt in [("orun_num_levels", i32), ("orun_top_is_gamma", i32), ("orun_K", i32),
                              ("orun_cost", i64), ("orun_num_parts", i32)]:
                 getattr(lib, name).argtypes = [vp]
@@ -123,12 +126,16 @@ class Run:
     and keeps every level's arrays for inspection."""
 
     def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None,
-                 incident=False):
-        """incident=True: Delta counts every incident hyperedge (in(n) = I(n))."""
+                 incident=False, outbound=False):
+        """incident=True: Delta counts every incident hyperedge (in(n) = I(n));
+        outbound=True: the hyperedges sourced in the part (in(n) = {e : src(e) = n})."""
         lib = _load()
         self._keep = [_i32(offsets), _i32(pins), _i32(node_weights), _i32(edge_weights)]
         h = ctypes.c_void_p()
-        create = lib.orun_create_incident if incident else lib.orun_create
+        if incident and outbound:
+            raise ValueError("incident and outbound are exclusive")
+        create = (lib.orun_create_incident if incident else
+                  lib.orun_create_outbound if outbound else lib.orun_create)
         rc = create(int(num_nodes), int(len(offsets) - 1), *[_p(a) for a in self._keep],
                     ctypes.byref(h))
         if rc:
@@ -137,8 +144,8 @@ class Run:
         self.num_nodes = int(num_nodes)
 
     @classmethod
-    def from_graph(cls, g, incident=False):
-        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, incident)
+    def from_graph(cls, g, incident=False, outbound=False):
+        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, incident, outbound)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -155,9 +162,21 @@ class Run:
         self.close()
 
     # ---- whole method ----
-    def partition(self, omega: int, delta: int, refine_passes: int = 1) -> Result:
+    def partition(self, omega: int, delta: int, refine_passes: int = 1, max_levels: int = 0,
+                  matching: int = 0) -> Result:
+        """max_levels > 0: coarsening stops after that many matchings (the
+        library's hgp_options.max_levels), a bounded prefix of the method.
+        matching = 1: the exact maximum-weight matching of the pairing
+        pseudo-forest instead of the paper's two walks."""
         lib = _load()
-        rc = lib.orun_partition(self._h, int(omega), int(delta), int(refine_passes))
+        if matching:
+            rc = lib.orun_partition_ex(self._h, int(omega), int(delta), int(refine_passes),
+                                       int(max_levels), int(matching))
+        elif max_levels:
+            rc = lib.orun_partition_cut(self._h, int(omega), int(delta), int(refine_passes),
+                                        int(max_levels))
+        else:
+            rc = lib.orun_partition(self._h, int(omega), int(delta), int(refine_passes))
         if rc:
             raise OracleError(rc, "partition")
         np_ = lib.orun_num_parts(self._h)
@@ -314,6 +333,7 @@ class Run:
 
 
 def match(pair, score, method: int = 0):
+    """method 0: the two walks; 1: the lock restatement; 2: exact DP."""
     pair = _i32(pair)
     score = _i32(score)
     out = np.empty(len(pair), dtype=np.int32)

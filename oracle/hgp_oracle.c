@@ -101,7 +101,7 @@ static int transpose(int32_t rows, int32_t cols, const int64_t *off,
  */
 static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
                         const int32_t *pins, const int32_t *nw, const int32_t *ew,
-                        int32_t incident, olevel *g, int32_t **src_out) {
+                        int32_t mode, olevel *g, int32_t **src_out) {
     if (N < 1 || E < 0 || !offsets || (E > 0 && !pins)) return ORC_INVALID;
     if (offsets[0] != 0) return ORC_INVALID;
     for (int32_t e = 0; e < E; ++e)
@@ -135,9 +135,10 @@ static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
     }
     int rc = transpose(E, N, g->poff, g->pins, &g->ioff, &g->inc);
     if (rc) { free(src); olevel_free(g); return rc; }
-    /* in(n): the same transpose restricted to destination pins.  With
-     * `incident` (the Delta variant that counts every incident hyperedge,
-     * which the paper calls a trivial generalisation) in(n) = I(n). */
+    /* in(n): the same transpose restricted to destination pins (mode 0).
+     * The paper calls the other directions a trivial generalisation: mode 1
+     * counts every incident hyperedge, in(n) = I(n); mode 2 the outbound
+     * ones, in(n) = {e : src(e) = n}. */
     int64_t *dcount = (int64_t *)calloc((size_t)E + 1, sizeof(int64_t));
     int32_t *dst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P > 0 ? P : 1));
     if (!dcount || !dst) { free(dcount); free(dst); free(src); olevel_free(g); return ORC_OOM; }
@@ -145,7 +146,7 @@ static int build_level0(int32_t N, int32_t E, const int32_t *offsets,
     for (int32_t e = 0; e < E; ++e) {
         dcount[e] = k;
         for (int64_t j = g->poff[e]; j < g->poff[e + 1]; ++j)
-            if (incident || g->pins[j] != src[e]) dst[k++] = g->pins[j];
+            if (mode == 1 || (mode == 0) == (g->pins[j] != src[e])) dst[k++] = g->pins[j];
     }
     dcount[E] = k;
     rc = transpose(E, N, dcount, dst, &g->noff, &g->in);
@@ -495,6 +496,88 @@ static int match_walks(int32_t V, const int32_t *pair, const int64_t *score, int
     }
     free(depth); free(order); free(stack); free(bucket);
     return ORC_OK;
+}
+
+/*
+ * Exact maximum-weight matching of the pairing pseudo-forest, the exact
+ * alternative to the two walks that the paper leaves as future work.
+ * Edges are {n, pair(n)} with weight score(n).  Every cycle is a root
+ * two-cycle {a, b} (Sec. III-A) whose two directed edges are one edge of
+ * weight score(a) = score(b); making b = max(a, b) a child of a = min(a, b)
+ * turns each component into a tree rooted at a.  Nodes with no candidate are
+ * roots without children.  With w(c) the weight of the edge from child c to
+ * its parent, children before parents:
+ *   up(v)   = sum over children c of best(c)   (v not matched below itself)
+ *   g(v)    = max over children c of w(c) - max(0, g(c)) (no term for a leaf):
+ *             what matching v to a child adds to up(v); c*(v) = the child
+ *             with the largest (that value, id)
+ *   best(v) = up(v) + max(0, g(v))
+ * and parents before children: a root is free; a free node v with g(v) > 0
+ * is matched to c*(v), which is then taken; all other nodes are left to
+ * their own subtree.  (A zero gain leaves v free.)  The matched weight is
+ * the sum of best over the roots, the maximum over all matchings.
+ */
+static int match_dp(int32_t V, const int32_t *pair, const int64_t *score, int32_t *match) {
+    int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+    int32_t *depth = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+    int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+    int32_t *cstar = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+    int64_t *up = (int64_t *)calloc((size_t)V, sizeof(int64_t));
+    int64_t *g = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+    int64_t *bucket = (int64_t *)calloc((size_t)V + 2, sizeof(int64_t));
+    signed char *taken = (signed char *)calloc((size_t)V, 1);
+    int rc = ORC_OK;
+    if (!par || !depth || !order || !stack || !cstar || !up || !g || !bucket || !taken) {
+        rc = ORC_OOM;
+        goto done;
+    }
+    for (int32_t n = 0; n < V; ++n) {
+        int32_t m = pair[n];
+        if (m < 0) par[n] = -1;
+        else if (pair[m] == n) par[n] = n < m ? -1 : m;     /* root two-cycle */
+        else par[n] = m;
+        cstar[n] = -1;
+        g[n] = 0;
+        depth[n] = par[n] < 0 ? 0 : -1;
+        match[n] = n;
+    }
+    for (int32_t n = 0; n < V; ++n) {               /* depth below the root */
+        int32_t sp = 0, x = n;
+        while (depth[x] < 0) {
+            if (sp >= V) { rc = ORC_INTERNAL; goto done; }
+            stack[sp++] = x;
+            x = par[x];
+        }
+        while (sp > 0) { int32_t y = stack[--sp]; depth[y] = depth[par[y]] + 1; }
+    }
+    for (int32_t n = 0; n < V; ++n) bucket[depth[n] + 1]++;
+    for (int32_t d = 0; d <= V; ++d) bucket[d + 1] += bucket[d];
+    for (int32_t n = 0; n < V; ++n) order[bucket[depth[n]]++] = n;
+    /* children before parents */
+    for (int32_t i = V - 1; i >= 0; --i) {
+        int32_t c = order[i], p = par[c];
+        if (p < 0) continue;
+        int64_t gc = cstar[c] >= 0 && g[c] > 0 ? g[c] : 0;
+        up[p] += up[c] + gc;                         /* best(c) */
+        int64_t gain = score[c] - gc;
+        if (cstar[p] < 0 || gain > g[p] || (gain == g[p] && c > cstar[p])) {
+            g[p] = gain;
+            cstar[p] = c;
+        }
+    }
+    /* parents before children */
+    for (int32_t i = 0; i < V; ++i) {
+        int32_t v = order[i];
+        if (taken[v] || cstar[v] < 0 || g[v] <= 0) continue;
+        match[v] = cstar[v];
+        match[cstar[v]] = v;
+        taken[cstar[v]] = 1;
+    }
+done:
+    free(par); free(depth); free(order); free(stack); free(cstar); free(up); free(g);
+    free(bucket); free(taken);
+    return rc;
 }
 
 /*
@@ -852,6 +935,12 @@ int orun_create_incident(int32_t N, int32_t E, const int32_t *offsets, const int
     return orun_create_mode(N, E, offsets, pins, node_w, edge_w, 1, out);
 }
 
+/* Delta counting the hyperedges whose source lies in the part. */
+int orun_create_outbound(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
+                         const int32_t *node_w, const int32_t *edge_w, orun **out) {
+    return orun_create_mode(N, E, offsets, pins, node_w, edge_w, 2, out);
+}
+
 static int orun_create_mode(int32_t N, int32_t E, const int32_t *offsets, const int32_t *pins,
                             const int32_t *node_w, const int32_t *edge_w, int32_t incident,
                             orun **out) {
@@ -927,7 +1016,12 @@ static int64_t connectivity(const olevel *g, const int32_t *ew, const int32_t *r
     return c;
 }
 
-static int partition_impl(orun *r, int64_t omega, int64_t delta, int32_t refine_passes) {
+/* max_levels > 0 stops coarsening after that many matchings, the clusters
+ * of the last one becoming the parts exactly as when the node target is
+ * reached; 0 applies the paper's stop rule alone.  (Not part of the method:
+ * a bounded prefix of it, for timing samples and large-input checks.) */
+static int partition_impl(orun *r, int64_t omega, int64_t delta, int32_t refine_passes,
+                          int32_t max_levels, int32_t matching) {
     if (omega < 1 || delta < 0 || refine_passes < 0) return ORC_INVALID;
     orun_clear(r);
     olevel *G0 = &r->G[0];
@@ -973,7 +1067,9 @@ static int partition_impl(orun *r, int64_t omega, int64_t delta, int32_t refine_
             if (rc) { free(mscore); goto fail; }
             for (int32_t n = 0; n < V; ++n)
                 mscore[n] = r->model ? learned_composite(r->key[l][n], r->score[l][n]) : r->score[l][n];
-            rc = match_walks(V, r->pair[l], mscore, r->match[l]);
+            /* matching 1: the exact maximum-weight matching (plain order only) */
+            rc = matching == 1 ? match_dp(V, r->pair[l], mscore, r->match[l])
+                               : match_walks(V, r->pair[l], mscore, r->match[l]);
             free(mscore);
             if (rc) goto fail;
             int32_t matched = 0;
@@ -987,7 +1083,7 @@ static int partition_impl(orun *r, int64_t omega, int64_t delta, int32_t refine_
             int32_t V2 = gamma_from_match(V, r->match[l], r->gamma[l]);
             /* Sec. III-B.4: once the target is reached the clusters become
              * the partitions without building another level. */
-            if (V2 <= target) {
+            if (V2 <= target || (max_levels > 0 && l + 1 >= max_levels)) {
                 r->K = V2;
                 r->top_is_gamma = 1;
                 break;
@@ -1085,7 +1181,24 @@ fail:
 /* The method as printed (Eq. (2) order). */
 int orun_partition(orun *r, int64_t omega, int64_t delta, int32_t refine_passes) {
     r->model = NULL;
-    return partition_impl(r, omega, delta, refine_passes);
+    return partition_impl(r, omega, delta, refine_passes, 0, 0);
+}
+
+/* The same, coarsening cut after max_levels matchings (see partition_impl). */
+int orun_partition_cut(orun *r, int64_t omega, int64_t delta, int32_t refine_passes,
+                       int32_t max_levels) {
+    if (max_levels < 0) return ORC_INVALID;
+    r->model = NULL;
+    return partition_impl(r, omega, delta, refine_passes, max_levels, 0);
+}
+
+/* With a choice of matching: 0 the two walks (Sec. III-B.3), 1 the exact
+ * maximum-weight matching of the pairing pseudo-forest (match_dp). */
+int orun_partition_ex(orun *r, int64_t omega, int64_t delta, int32_t refine_passes,
+                      int32_t max_levels, int32_t matching) {
+    if (max_levels < 0 || matching < 0 || matching > 1) return ORC_INVALID;
+    r->model = NULL;
+    return partition_impl(r, omega, delta, refine_passes, max_levels, matching);
 }
 
 /* The same with the learned candidate order (model as bfloat16 bits). */
@@ -1096,7 +1209,7 @@ int orun_partition_learned(orun *r, int64_t omega, int64_t delta, int32_t refine
     int rc = model_from_bits(w1, b1, w2, b2, key_bits, &M);
     if (rc) return rc;
     r->model = &M;
-    rc = partition_impl(r, omega, delta, refine_passes);
+    rc = partition_impl(r, omega, delta, refine_passes, 0, 0);
     r->model = NULL;
     return rc;
 }
@@ -1242,17 +1355,21 @@ int orun_score0_nodes(const orun *r, int64_t omega, int64_t delta, const int32_t
 
 /* Matching of an arbitrary pairing graph; method 0 = the two walks,
  * method 1 = the lock recursion. */
+int oracle_match64(int32_t V, const int32_t *pair, const int64_t *score, int32_t method, int32_t *match);
+
 int oracle_match(int32_t V, const int32_t *pair, const int32_t *score, int32_t method, int32_t *match) {
     int64_t *s64 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V > 0 ? V : 1));
     if (!s64) return ORC_OOM;
     for (int32_t n = 0; n < V; ++n) s64[n] = score[n];
-    int rc = method == 0 ? match_walks(V, pair, s64, match) : match_locks(V, pair, s64, match);
+    int rc = oracle_match64(V, pair, s64, method, match);
     free(s64);
     return rc;
 }
 
-/* Same with int64 scores (the learned order's composite keys). */
+/* Same with int64 scores (the learned order's composite keys).
+ * method 0: the two walks; 1: the lock restatement; 2: exact DP. */
 int oracle_match64(int32_t V, const int32_t *pair, const int64_t *score, int32_t method, int32_t *match) {
+    if (method == 2) return match_dp(V, pair, score, match);
     return method == 0 ? match_walks(V, pair, score, match) : match_locks(V, pair, score, match);
 }
 

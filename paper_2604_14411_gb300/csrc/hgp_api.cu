@@ -29,11 +29,14 @@ cudaError_t run_fill_baseline(Arena &ar, const Level &L0, int64_t omega, int64_t
 cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
                       const int32_t *key, int32_t *match, int32_t *gamma, int32_t *d_V2,
                       int32_t *status, cudaStream_t s);
-cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
-                         const int32_t *pair, const int32_t *score, int32_t *status,
-                         cudaStream_t s);
+cudaError_t run_contract(Arena &keep, Arena &inc_ar, Arena &roll, Arena &tmp, const Level &L,
+                         int32_t V2, Level &H, const int32_t *pair, const int32_t *score,
+                         int32_t *status, cudaStream_t s, PropTiming *kt);
+cudaError_t run_rebuild_incidence(Arena &ar, const Level &L, int32_t **ioff, int32_t **inc,
+                                  cudaStream_t s);
 int run_build_level0(Arena &keep, Arena &tmp, int32_t N, int32_t E, Level &L, const int32_t *ew,
-                     int64_t *wsum_e, cudaError_t *cerr, std::string *why, cudaStream_t s);
+                     int32_t delta_mode, int64_t *wsum_e, cudaError_t *cerr, std::string *why,
+                     cudaStream_t s);
 cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64_t wsum,
                             int32_t *rho, int32_t K, int64_t omega, int64_t delta,
                             long long *d_stats, unsigned long long *d_applied, uint32_t debug,
@@ -72,6 +75,8 @@ using namespace hgp;
 
 struct hgp_graph {
     cudaStream_t stream = nullptr;
+    hgp_allocator allocator{};
+    bool has_allocator = false;
     Arena keep;
     Level L0;
     int32_t *ew = nullptr;
@@ -82,6 +87,7 @@ struct hgp_graph {
     std::string err;
     hgp_stats stats{};
     std::vector<std::vector<int64_t>> dbg[10];
+    const hgp_allocator *user_allocator() const { return has_allocator ? &allocator : nullptr; }
 };
 
 static int fail(hgp_graph *g, int code, const std::string &msg) {
@@ -111,19 +117,27 @@ static thread_local std::string t_create_err;
 
 extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *offsets,
                           const int32_t *pins, const int32_t *node_weights,
-                          const int32_t *edge_weights, uint32_t flags, void *stream,
-                          hgp_graph **out) {
+                          const int32_t *edge_weights, uint32_t flags,
+                          const hgp_allocator *alloc, void *stream, hgp_graph **out) {
     if (!out) return HGP_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_nodes < 1 || num_edges < 0 || !offsets || (num_edges > 0 && !pins))
         return HGP_ERR_INVALID_ARG;
-    if ((flags & ~(HGP_INPUT_DEVICE | HGP_DELTA_INCIDENT)) != 0) return HGP_ERR_INVALID_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return HGP_ERR_INVALID_ARG;
+    if ((flags & ~(HGP_INPUT_DEVICE | HGP_DELTA_INCIDENT | HGP_DELTA_OUTBOUND)) != 0)
+        return HGP_ERR_INVALID_ARG;
+    if ((flags & HGP_DELTA_INCIDENT) && (flags & HGP_DELTA_OUTBOUND)) return HGP_ERR_INVALID_ARG;
     double t0 = now_ms();
     int64_t launches0 = g_launches;
     hgp_graph *g = new (std::nothrow) hgp_graph();
     if (!g) return HGP_ERR_OOM;
     g->stream = (cudaStream_t)stream;
+    if (alloc) {
+        g->allocator = *alloc;
+        g->has_allocator = true;
+    }
     g->keep.stream = g->stream;
+    g->keep.user = g->user_allocator();
     g->N = num_nodes;
     g->E = num_edges;
     cudaStream_t s = g->stream;
@@ -132,8 +146,12 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
     Level &L = g->L0;
     L.V = num_nodes;
     L.E = num_edges;
+    Arena tmp;
+    tmp.stream = s;
+    tmp.user = g->user_allocator();
     auto bail = [&](int code) {
         cudaStreamSynchronize(s);
+        tmp.release_all();
         g->keep.release_all();
         cudaStreamSynchronize(s);
         t_create_err = g->err;
@@ -177,19 +195,11 @@ extern "C" int hgp_create(int32_t num_nodes, int32_t num_edges, const int32_t *o
         else
             fill_i32(g->ew, 1, num_edges, s);
     }
-    Arena tmp;
-    tmp.stream = s;
     cudaError_t ce = cudaSuccess;
     std::string why;
-    int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, &g->wsum_e, &ce, &why, s);
-    if (rc == 0 && (flags & HGP_DELTA_INCIDENT)) {
-        // Delta counts every incident hyperedge: in(n) = I(n), and every pin
-        // (the source's node included) is a destination at every level
-        L.noff = L.ioff;
-        L.inn = L.inc;
-        L.Q = L.P;
-        if (num_edges > 0) CKC(cudaMemsetAsync(L.sdst, 1, (size_t)num_edges, s), "incident flags");
-    }
+    const int32_t delta_mode = (flags & HGP_DELTA_INCIDENT) ? 1 : (flags & HGP_DELTA_OUTBOUND) ? 2 : 0;
+    int rc = run_build_level0(g->keep, tmp, num_nodes, num_edges, L, g->ew, delta_mode, &g->wsum_e,
+                              &ce, &why, s);
     if (rc != 0) {
         tmp.release_all();
         if (rc < 0) return bail(cuda_fail(g, ce, "build level 0"));
@@ -294,7 +304,8 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         if (opt->max_levels < 0) return fail(g, HGP_ERR_INVALID_ARG, "max_levels must be >= 0");
         max_levels = opt->max_levels;
         if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
-                                     HGP_DEBUG_NO_BITMAP | HGP_DEBUG_FORCE_CLUSTER))
+                                     HGP_DEBUG_NO_BITMAP | HGP_DEBUG_FORCE_CLUSTER |
+                                     HGP_DEBUG_SMALL_TABLE | HGP_DEBUG_REBUILD_INC))
             return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
         passes = opt->refine_passes;
         debug = opt->debug;
@@ -304,21 +315,46 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         return fail(g, HGP_ERR_INFEASIBLE, "a single node exceeds omega or delta; no partition exists");
     double t0 = now_ms();
     int64_t launches0 = g_launches;
-    Arena lv, tmp;
-    lv.stream = s;
-    tmp.stream = s;
-    lv.min_chunk = (size_t)64 << 20;
-    tmp.min_chunk = (size_t)64 << 20;
+    // Storage of the hierarchy:
+    //   lv       what refinement reads at every level (weights, pins, sources,
+    //            gamma, match) and I(n) while it fits the budget below
+    //   roll[2]  in(n) and the carried scoring state (and I(n) past the
+    //            budget): level l's live in roll[l & 1] and die when level
+    //            l + 2 is built, so only two levels of them exist at a time
+    //   rb       I(n) rebuilt from the pins when refinement reaches a level
+    //            whose copy was not kept
+    Arena lv, tmp, roll[2], rb;
+    for (Arena *a : {&lv, &tmp, &roll[0], &roll[1], &rb}) {
+        a->stream = s;
+        a->user = g->user_allocator();
+        a->min_chunk = (size_t)64 << 20;
+    }
+    size_t inc_budget = 0, inc_kept = 0;
+    if (!(debug & HGP_DEBUG_REBUILD_INC)) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) inc_budget = fr / 10 * 4;   // 40 % of free
+    }
     Timer tm;
     tm.on = (debug & HGP_DEBUG_TIMING) != 0;
     tm.s = s;
+    PropTiming ctime;                  // contraction kernels (timing runs)
+    PropTiming ptime;                  // proposal kernels (timing runs)
+    auto drop_events = [&]() {
+        for (PropTiming *t : {&ptime, &ctime}) {
+            for (auto &pr : t->ev) {
+                if (pr.first) cudaEventDestroy(pr.first);
+                if (pr.second) cudaEventDestroy(pr.second);
+            }
+            t->ev.clear();
+        }
+    };
     if (debug & HGP_DEBUG_KEEP_LEVELS)
         for (auto &v : g->dbg) v.clear();
     auto cleanup = [&]() {
         cudaStreamSynchronize(s);
-        tmp.release_all();
-        lv.release_all();
+        for (Arena *a : {&tmp, &lv, &roll[0], &roll[1], &rb}) a->release_all();
         cudaStreamSynchronize(s);
+        drop_events();
     };
 #define CKP(expr, where)                                        \
     do {                                                        \
@@ -397,9 +433,26 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
                 break;
             }
             Level H;
+            // level l + 1's in(n) and scoring state reuse the storage of
+            // level l - 1's, which nothing reads any more
+            Arena &ra = roll[(l + 1) & 1];
+            ra.reset();
+            if (l >= 1) {
+                Level &O = levels[l - 1];
+                O.noff = O.inn = nullptr;
+                O.dead = O.merged = nullptr;
+                O.thr = nullptr;
+                O.old_id = nullptr;
+                if (O.inc_rolling) O.ioff = O.inc = nullptr;
+            }
+            const size_t inc_bytes = 4 * ((size_t)L.P + (size_t)L.V + 1) + 512;   // H.P <= L.P
+            const bool keep_inc = inc_kept + inc_bytes <= inc_budget;
+            if (keep_inc) inc_kept += inc_bytes;
             tm.start(2, &ev_a);
-            CKP(run_contract(lv, tmp, L, V2, H, pair, score, d_status, s), "contract");
+            CKP(run_contract(lv, keep_inc ? lv : ra, ra, tmp, L, V2, H, pair, score, d_status, s,
+                             tm.on ? &ctime : nullptr), "contract");
             tm.stop(2, ev_a);
+            H.inc_rolling = !keep_inc;
             levels.push_back(H);
             pins_total += H.P;
             tmp.reset();               // stream order keeps the reuse safe
@@ -418,7 +471,6 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         iota_i32(rho, levels[L].V, s);
     long long *d_rstat = nullptr;
     unsigned long long *d_applied = nullptr;
-    PropTiming ptime;
     CKP(dalloc(lv, &ptime.bytes, 1), "alloc");
     CKP(cudaMemsetAsync(ptime.bytes, 0, sizeof(unsigned long long), s), "memset");
     CKP(dalloc(lv, &d_rstat, 3 * levels.size()), "alloc");
@@ -434,7 +486,11 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     CKP(dalloc(lv, &d_flag, 1), "alloc");
     CKP(cudaMemsetAsync(d_flag, 0, sizeof(int32_t), s), "memset");
     for (int l = L; l >= 0; --l) {
-        const Level &Lv = levels[l];
+        Level &Lv = levels[l];
+        if (!Lv.inc) {                // I(n) was not kept: rebuild it from the pins
+            rb.reset();
+            CKP(run_rebuild_incidence(rb, Lv, &Lv.ioff, &Lv.inc, s), "rebuild incidence");
+        }
         if (debug & HGP_DEBUG_KEEP_LEVELS) keep_array(g, HGP_LEVEL_RHO_IN, l, rho, Lv.V, s);
         for (int p = 0; p < passes; ++p) {
             PropReuse ru;
@@ -549,8 +605,16 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         unsigned long long pb = 0;
         cudaMemcpy(&pb, ptime.bytes, sizeof(pb), cudaMemcpyDeviceToHost);
         st.propose_bytes = (int64_t)pb;
+        double tc = 0;
+        for (auto &pr : ctime.ev) {
+            float ms = 0;
+            cudaEventSynchronize(pr.second);
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            tc += ms;
+        }
+        st.ms_contract_kernels = tc;
+        st.contract_bytes = (int64_t)ctime.host_bytes;
     }
-    for (auto &pr : ptime.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     (void)c0; (void)c1;
     st.kernel_launches = g_launches - launches0;
     cleanup();
@@ -575,6 +639,7 @@ extern "C" int hgp_fill_baseline(hgp_graph *g, int64_t omega, int64_t delta, hgp
     cudaStream_t s = g->stream;
     Arena tmp;
     tmp.stream = s;
+    tmp.user = g->user_allocator();
     auto done = [&](cudaError_t e, const char *where) {
         cudaStreamSynchronize(s);
         tmp.release_all();

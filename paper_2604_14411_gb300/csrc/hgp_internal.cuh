@@ -25,7 +25,11 @@ enum DevStatus : int32_t {
 //   I(n)     : ioff[V+1], inc[P]   incident hyperedges, ascending
 //   in(n)    : noff[V+1], inn[Q]   inbound hyperedges, ascending
 //   src[e]   : the level's node holding the source of e
-//   sdst[e]  : 1 when src[e] is also a destination of e at this level
+//   sdst[e]  : role byte of e for the Delta count (see counts_in): bit 0 --
+//              the node holding the source has e in its in(); bit 1 -- every
+//              other node of e does.  Inbound Delta (the paper's): 2, plus 1
+//              once the source's node also holds a destination; incident: 3;
+//              outbound: 1
 struct Level {
     int32_t V = 0, E = 0;
     int64_t P = 0, Q = 0;
@@ -50,16 +54,21 @@ struct Level {
     uint8_t *dead = nullptr, *merged = nullptr;
     unsigned long long *thr = nullptr;
     int32_t *old_id = nullptr;
+    // I(n) lives with in(n) in storage that the next-but-one contraction
+    // reuses; refinement then rebuilds it from the pins
+    bool inc_rolling = false;
 };
 
 // ---------------- stream-ordered device memory ----------------
-// Bump allocator over device chunks obtained with cudaMallocAsync on
-// `stream`.  reset() makes every allocation dead and reuses the chunks from
-// the start; this is safe because all work runs in order on the one stream.
-// With min_chunk = 0 every allocation gets an exact chunk of its own.
+// Bump allocator over device chunks obtained on `stream` from the handle's
+// hgp_allocator (cudaMallocAsync / cudaFreeAsync when it has none).  reset()
+// makes every allocation dead and reuses the chunks from the start; this is
+// safe because all work runs in order on the one stream.  With min_chunk = 0
+// every allocation gets an exact chunk of its own.
 struct Arena {
     struct Chunk { char *base; size_t size; };
     cudaStream_t stream = nullptr;
+    const hgp_allocator *user = nullptr;   // null: cudaMallocAsync / cudaFreeAsync
     size_t min_chunk = 0;
     std::vector<Chunk> chunks;
     size_t cur = 0, off = 0;
@@ -73,9 +82,11 @@ inline cudaError_t dalloc(Arena &a, T **p, size_t count) {
     return a.alloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
 }
 
-// Event pairs around every proposal launch of a partition (timing runs).
+// Event pairs around every proposal launch (or contraction phase) of a
+// partition (timing runs), with the algorithmic bytes they move.
 struct PropTiming {
     unsigned long long *bytes = nullptr;   // device counter
+    unsigned long long host_bytes = 0;     // counted on the host
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 
@@ -133,6 +144,12 @@ inline int bits_for(int64_t maxval) {   // bits to hold values in [0, maxval]
 // ---------------- device helpers ----------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+// Whether level node m has hyperedge e in its in() (the set Delta counts),
+// from e's source node and role byte.
+__device__ __forceinline__ bool counts_in(int32_t m, int32_t src_e, uint8_t role) {
+    return (m == src_e) ? (role & 1) != 0 : (role & 2) != 0;
+}
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
     atomicCAS(status, 0, code);

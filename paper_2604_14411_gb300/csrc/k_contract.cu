@@ -213,7 +213,10 @@ __global__ void k_coarse_src(int32_t E, const int32_t *src, const uint8_t *sdst,
         int32_t e = (int32_t)i;
         int32_t s = gamma[src[e]];
         src2[e] = s;
-        sdst2[e] = (sdst[e] || contains_sorted(inn2, noff2[s], noff2[s + 1], e)) ? 1 : 0;
+        // bit 1 is fixed by the Delta mode; bit 0 turns on once the source's
+        // coarse node has e in its in() (a merged destination, inbound mode)
+        const uint8_t r = sdst[e];
+        sdst2[e] = (uint8_t)((r & 2) | (((r & 1) || contains_sorted(inn2, noff2[s], noff2[s + 1], e)) ? 1 : 0));
     }
 }
 
@@ -230,11 +233,30 @@ static int grid1d(int64_t n) {
 }
 
 // Builds level `H` (V2 nodes) from level `L` and its match/gamma.  Device
-// allocations of H go to `keep`; temporaries to `tmp`.
-cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Level &H,
-                         const int32_t *pair, const int32_t *score, int32_t *status,
-                         cudaStream_t s) {
+// allocations of H go to `keep` (what refinement reads: weights, pins,
+// sources), `inc_ar` (I(n)) and `roll` (in(n) and the state carried into the
+// next scoring, dead once H itself is contracted); temporaries to `tmp`.
+// With `kt` set, CUDA events bracket the two kernel phases (count, write) so
+// that their device time excludes the host read of the new sizes between
+// them, and kt->host_bytes gains the contraction's algorithmic bytes: per
+// level 4 B per pin read, gamma-gathered and written (pins), 4 B per entry
+// read and written (I, in), and 12 B per hyperedge and per node (offsets).
+cudaError_t run_contract(Arena &keep, Arena &inc_ar, Arena &roll, Arena &tmp, const Level &L,
+                         int32_t V2, Level &H, const int32_t *pair, const int32_t *score,
+                         int32_t *status, cudaStream_t s, PropTiming *kt) {
     cudaError_t e;
+    auto ev_begin = [&]() {
+        if (!kt) return;
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, s);
+        kt->ev.push_back({a, nullptr});
+    };
+    auto ev_end = [&]() {
+        if (!kt) return;
+        cudaEventCreate(&kt->ev.back().second);
+        cudaEventRecord(kt->ev.back().second, s);
+    };
     H.V = V2;
     H.E = L.E;
     int32_t *rep_of = nullptr, *cntI = nullptr, *cntN = nullptr, *cntP = nullptr, *dmax = nullptr;
@@ -247,16 +269,17 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (!e) e = dalloc(tmp, &cntN, V2);
     if (!e) e = dalloc(tmp, &cntP, L.E);
     if (!e) e = dalloc(keep, &H.w, V2);
-    if (!e) e = dalloc(keep, &H.ioff, (size_t)V2 + 1);
-    if (!e) e = dalloc(keep, &H.noff, (size_t)V2 + 1);
+    if (!e) e = dalloc(inc_ar, &H.ioff, (size_t)V2 + 1);
+    if (!e) e = dalloc(roll, &H.noff, (size_t)V2 + 1);
     if (!e) e = dalloc(keep, &H.poff, (size_t)L.E + 1);
     if (!e) e = dalloc(keep, &H.src, L.E);
     if (!e) e = dalloc(keep, &H.sdst, L.E);
-    if (!e) e = dalloc(keep, &H.dead, V2);
-    if (!e) e = dalloc(keep, &H.merged, V2);
-    if (!e) e = dalloc(keep, &H.thr, V2);
-    if (!e) e = dalloc(keep, &H.old_id, V2);
+    if (!e) e = dalloc(roll, &H.dead, V2);
+    if (!e) e = dalloc(roll, &H.merged, V2);
+    if (!e) e = dalloc(roll, &H.thr, V2);
+    if (!e) e = dalloc(roll, &H.old_id, V2);
     if (e) return e;
+    ev_begin();
     k_coarse_nodes<<<grid1d(L.V), 256, 0, s>>>(L.V, L.match, L.gamma, L.w, rep_of, H.w);
     count_launch();
     k_carry<<<grid1d(L.V), 256, 0, s>>>(L.V, pair, score, L.match, L.gamma, L.dead, H.dead,
@@ -285,6 +308,7 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     if (!e) e = counts_to_offsets(tmp, cntN, H.noff, V2, s);
     if (!e) e = counts_to_offsets(tmp, cntP, H.poff, L.E, s);
     if (e) return e;
+    ev_end();
     int32_t tot[5];
     e = cudaMemcpyAsync(&tot[3], dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&tot[4], dmax + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -298,10 +322,11 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     H.Q = tot[1];
     H.max_in = tot[3];
     H.max_edge = tot[4];
-    e = dalloc(keep, &H.inc, H.P);
-    if (!e) e = dalloc(keep, &H.inn, H.Q);
+    e = dalloc(inc_ar, &H.inc, H.P);
+    if (!e) e = dalloc(roll, &H.inn, H.Q);
     if (!e) e = dalloc(keep, &H.pins, H.P);
     if (e) return e;
+    ev_begin();
     {
         int blocks = V2 < num_sms() * 16 ? V2 : num_sms() * 16;
         k_union_copy<<<blocks, 256, 0, s>>>(V2, rep_of, L.match, L.ioff, L.inc, L.noff, L.inn,
@@ -319,6 +344,12 @@ cudaError_t run_contract(Arena &keep, Arena &tmp, const Level &L, int32_t V2, Le
     k_coarse_src<<<grid1d(L.E), 256, 0, s>>>(L.E, L.src, L.sdst, L.gamma, H.noff, H.inn, H.src,
                                              H.sdst);
     count_launch();
+    ev_end();
+    if (kt)
+        kt->host_bytes += 4ull * (unsigned long long)(3 * L.P + H.P) +      // pins
+                          4ull * (unsigned long long)(L.P + H.P) +          // I
+                          4ull * (unsigned long long)(L.Q + H.Q) +          // in
+                          12ull * (unsigned long long)((int64_t)L.E + L.V);  // offsets
     (void)status;
     return cudaGetLastError();
 }

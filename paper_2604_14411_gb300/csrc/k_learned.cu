@@ -265,11 +265,11 @@ k_score_learned(LearnedArgs a, MlpParams M) {
                 const int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
                 const int32_t s_e = __shfl_sync(0xffffffffu, se, t);
                 const int32_t sd_e = __shfl_sync(0xffffffffu, sd, t);
-                const bool n_in = s_e != n || sd_e;     // e in in(n)
+                const bool n_in = counts_in(n, s_e, (uint8_t)sd_e);     // e in in(n)
                 for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
                     const int32_t m = a.pins[j];
                     if (m == n) continue;
-                    const int32_t both = (n_in && (m != s_e || sd_e)) ? 1 : 0;
+                    const int32_t both = (n_in && counts_in(m, s_e, (uint8_t)sd_e)) ? 1 : 0;
                     if (DENSE) {
                         atomicAdd(&hist[m], wt);
                         if (both) atomicAdd(&inter[m], 1);
@@ -383,11 +383,11 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
                 const int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
                 const int32_t s_e = __shfl_sync(0xffffffffu, se, t);
                 const int32_t sd_e = __shfl_sync(0xffffffffu, sd, t);
-                const bool n_in = s_e != n || sd_e;
+                const bool n_in = counts_in(n, s_e, (uint8_t)sd_e);
                 for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
                     const int32_t m = a.pins[j];
                     if (m == n) continue;
-                    const uint32_t both = (n_in && (m != s_e || sd_e)) ? 1u : 0u;
+                    const uint32_t both = (n_in && counts_in(m, s_e, (uint8_t)sd_e)) ? 1u : 0u;
                     const int32_t owner = m / slice;
                     atomicAdd(cl.map_shared_rank(cnt, owner) + (m - owner * slice), (wt << 16) | both);
                 }
@@ -508,8 +508,9 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
         e = allow_dynamic_smem(k_score_learned<true>);
         if (e) return e;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_learned<true>, kLearnThreads,
-                                                      dense_smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_learned<true>,
+                                                          kLearnThreads, dense_smem);
+        if (e) return e;
         if (per_sm < 1) per_sm = 1;
         int blocks = sms * per_sm;
         if (blocks > L.V) blocks = L.V;

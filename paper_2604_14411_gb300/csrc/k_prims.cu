@@ -45,6 +45,8 @@ int num_sms() {
 
 cudaError_t Arena::alloc(void **p, size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
+    // chunks from `empty` on hold nothing allocated since the last reset
+    size_t empty = off == 0 ? cur : cur + 1;
     while (cur < chunks.size()) {
         if (off + bytes <= chunks[cur].size) {
             *p = chunks[cur].base + off;
@@ -54,10 +56,27 @@ cudaError_t Arena::alloc(void **p, size_t bytes) {
         ++cur;
         off = 0;
     }
-    size_t sz = bytes > min_chunk ? bytes : min_chunk;
+    // None of them fits.  Return them instead of keeping them: every earlier
+    // use of them was enqueued on the stream before this point.  (Keeping them
+    // let an arena grow without bound when allocation sizes creep upwards from
+    // cycle to cycle, as they do when refinement walks from coarse to fine
+    // levels.)  Pooled chunks get 1/8 slack for the same reason.
+    for (size_t i = empty; i < chunks.size(); ++i) {
+        if (user) user->free(user->ctx, chunks[i].base, chunks[i].size, stream);
+        else cudaFreeAsync(chunks[i].base, stream);
+    }
+    if (empty < chunks.size()) chunks.resize(empty);
+    size_t sz = min_chunk ? bytes + (bytes >> 3) : bytes;
+    if (sz < min_chunk) sz = min_chunk;
+    sz = (sz + 255) & ~(size_t)255;
     void *b = nullptr;
-    cudaError_t e = cudaMallocAsync(&b, sz, stream);
-    if (e != cudaSuccess) return e;
+    if (user) {
+        b = user->alloc(user->ctx, sz, stream);
+        if (!b) return cudaErrorMemoryAllocation;
+    } else {
+        cudaError_t e = cudaMallocAsync(&b, sz, stream);
+        if (e != cudaSuccess) return e;
+    }
     chunks.push_back({static_cast<char *>(b), sz});
     cur = chunks.size() - 1;
     off = bytes;
@@ -66,7 +85,10 @@ cudaError_t Arena::alloc(void **p, size_t bytes) {
 }
 
 void Arena::release_all() {
-    for (auto &c : chunks) cudaFreeAsync(c.base, stream);
+    for (auto &c : chunks) {
+        if (user) user->free(user->ctx, c.base, c.size, stream);
+        else cudaFreeAsync(c.base, stream);
+    }
     chunks.clear();
     cur = off = 0;
 }

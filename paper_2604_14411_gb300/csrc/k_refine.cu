@@ -113,12 +113,15 @@ __global__ void k_runs(int32_t E, const int32_t *poff, PartsView pv,
         }
         __syncwarp();
         int32_t srcpart = rho[src[e]];
-        bool src_only_out = !sdst[e];
+        const uint8_t role = sdst[e];
         for (int32_t q = lane_id(); q < r; q += 32) {
             int32_t end = (q + 1 < r) ? rpos[p0 + q + 1] : p1;
             int32_t c = end - rpos[p0 + q];
             int32_t p = rpart[p0 + q];
-            int32_t ci = c - ((p == srcpart && src_only_out) ? 1 : 0);
+            // pins of the run that have e in their in(): the source's node by
+            // bit 0 of the role, every other node by bit 1
+            const int32_t has_src = p == srcpart ? 1 : 0;
+            int32_t ci = ((role & 2) ? c - has_src : 0) + ((role & 1) ? has_src : 0);
             rcnt[p0 + q] = c;
             rcin[p0 + q] = ci;
             if (inb && ci > 0) atomicAdd(use_smem ? &inb_s[p] : &inb[p], 1);
@@ -410,7 +413,7 @@ __global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_p
         int32_t base = evoff[k], i0 = ioff[n], d = ioff[n + 1] - i0;
         for (int32_t t = lane_id(); t < d; t += 32) {
             int32_t e = inc[i0 + t];
-            uint8_t isdst = (n != src[e] || sdst[e]) ? 1 : 0;
+            uint8_t isdst = counts_in(n, src[e], sdst[e]) ? 1 : 0;
             int32_t j = base + 2 * t;
             ev_p[j] = (uint32_t)ps;  ev_e[j] = e; ev_k[j] = (int32_t)k; ev_dst[j] = isdst; ev_id[j] = j;
             ev_p[j + 1] = (uint32_t)pd; ev_e[j + 1] = e; ev_k[j + 1] = (int32_t)k; ev_dst[j + 1] = isdst;
@@ -454,7 +457,7 @@ k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *i
     for (int64_t e = gw; e < E; e += nw) {
         int32_t p0 = poff[e], p1 = poff[e + 1];
         int32_t se = src[e];
-        bool sd = sdst[e] != 0;
+        const uint8_t role = sdst[e];
         int32_t cnt = 0;
         for (int32_t base = p0; base < p1; base += 32) {
             int32_t j = base + lane_id();
@@ -464,7 +467,7 @@ k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *i
             if (k >= 0) {
                 int32_t q = cnt + __popc(ball & lt);
                 sk[w][q] = k; sps[w][q] = mv_ps[k]; spd[w][q] = mv_pd[k]; sn[w][q] = m;
-                sdt[w][q] = (m != se || sd) ? 1 : 0;
+                sdt[w][q] = counts_in(m, se, role) ? 1 : 0;
             }
             cnt += __popc(ball);
         }
@@ -800,7 +803,8 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         e = allow_dynamic_smem(k_propose<true>);
         if (e) return e;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true>, kPropThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true>, kPropThreads, smem);
+        if (e) return e;
         if (per_sm < 1) per_sm = 1;
         int blocks = sms * per_sm;
         if (blocks > V) blocks = V;

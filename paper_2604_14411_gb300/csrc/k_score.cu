@@ -25,6 +25,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     a.omega = omega; a.delta = delta;
     a.pair = pair; a.score = score; a.status = status; a.bytes = bytes;
     a.dead = L.dead; a.merged = L.merged; a.thr = L.thr; a.old_id = L.old_id;
+    a.vec_pins = 1;      // level pins live in arena chunks: 256-byte aligned, sizes rounded to 256
     cudaError_t e = dalloc(ar, &a.next, 1);
     if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
     if (e) return e;
@@ -54,7 +55,9 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
         e = allow_dynamic_smem(k_score<true>);
         if (e) return e;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, dense_smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads,
+                                                          dense_smem);
+        if (e) return e;
         if (per_sm < 1) per_sm = 1;
         int blocks = sms * per_sm;
         if (blocks > L.V) blocks = L.V;
@@ -80,7 +83,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     if (e) return e;
     unsigned long long distinct = h_work < (unsigned long long)L.V ? h_work : (unsigned long long)L.V;
     unsigned long long gcap = 64;
-    while (gcap < 2 * distinct) gcap <<= 1;
+    while (gcap < 2 * distinct && !(debug & HGP_DEBUG_SMALL_TABLE)) gcap <<= 1;
     if (gcap > (1ull << 30)) return cudaErrorMemoryAllocation;
     a.gcap = (int32_t)gcap;
     e = allow_dynamic_smem(k_score<false>);

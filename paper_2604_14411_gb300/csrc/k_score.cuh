@@ -48,6 +48,8 @@ struct ScoreArgs {
     const unsigned long long *thr;
     const int32_t *old_id;
     int32_t *next;                   // work counter: nodes are taken dynamically
+    int32_t vec_pins;                // pins readable as 16-byte vectors: 16-byte aligned, and
+                                     // the allocation extends to a multiple of 16 bytes
 };
 
 // m is worth checking for n: alive, and either newly merged or ranked below
@@ -75,6 +77,77 @@ __device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
 #pragma unroll
     for (int i = 1; i < kScoreWarps; ++i) r = max(r, red[i]);
     return r;
+}
+
+// Eq. (2) accumulation over the hyperedges of I(n) that one warp owns
+// (entries i0 + first + stride * r of inc, r < count): add(m, omega(e)) for
+// every pin m != n of each.  Each lane first fetches one hyperedge's
+// (omega, pin range); then four hyperedges at a time, every lane loads its
+// 16-byte slice of each before any of its adds, so a warp keeps up to 2 KB
+// of pin loads in flight instead of one 128-byte load per hyperedge (the
+// loop is otherwise bound by load latency).  Slices are aligned to 4 pins
+// and masked to the hyperedge's range.  With vec_pins = 0 pins are read one
+// per lane.
+constexpr int kAccEdges = 4;
+
+template <typename Add>
+__device__ __forceinline__ void warp_accumulate(const ScoreArgs &a, int32_t n, int32_t i0,
+                                                int32_t first, int32_t stride, int32_t count,
+                                                Add &&add, unsigned long long &bytes) {
+    const int lane = lane_id();
+    for (int32_t r0 = 0; r0 < count; r0 += 32) {
+        int32_t we = 0, p0 = 0, p1 = 0;
+        if (r0 + lane < count) {
+            const int32_t e = a.inc[i0 + first + stride * (r0 + lane)];
+            we = a.ew[e];
+            p0 = a.poff[e];
+            p1 = a.poff[e + 1];
+        }
+        const int32_t cnt = min(32, count - r0);     // lanes >= cnt hold empty ranges
+        if (!a.vec_pins) {
+            for (int32_t t = 0; t < cnt; ++t) {
+                const int32_t wt = __shfl_sync(0xffffffffu, we, t);
+                const int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
+                const int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
+                for (int32_t j = b0 + lane; j < b1; j += 32) {
+                    const int32_t m = a.pins[j];
+                    if (m != n) add(m, wt);
+                }
+                if (lane == 0) bytes += 16ull + 4ull * (unsigned long long)(b1 - b0);
+            }
+            continue;
+        }
+        const int4 *pv = reinterpret_cast<const int4 *>(a.pins);
+        for (int32_t t = 0; t < cnt; t += kAccEdges) {
+            int32_t wt[kAccEdges], q0[kAccEdges], b0[kAccEdges], b1[kAccEdges];
+            int32_t span = 0;
+#pragma unroll
+            for (int u = 0; u < kAccEdges; ++u) {
+                const int src = (t + u) & 31;            // t + u < 32; past cnt: empty range
+                wt[u] = __shfl_sync(0xffffffffu, we, src);
+                b0[u] = __shfl_sync(0xffffffffu, p0, src);
+                b1[u] = __shfl_sync(0xffffffffu, p1, src);
+                if (t + u >= cnt) b0[u] = b1[u] = 0;
+                q0[u] = b0[u] >> 2;
+                span = max(span, ((b1[u] + 3) >> 2) - q0[u]);
+                if (lane == 0) bytes += t + u < cnt ? 16ull + 4ull * (unsigned long long)(b1[u] - b0[u]) : 0ull;
+            }
+            for (int32_t k = lane; k < span; k += 32) {
+                int4 v[kAccEdges];
+#pragma unroll
+                for (int u = 0; u < kAccEdges; ++u)
+                    v[u] = 4 * (q0[u] + k) < b1[u] ? pv[q0[u] + k] : make_int4(-1, -1, -1, -1);
+#pragma unroll
+                for (int u = 0; u < kAccEdges; ++u) {
+                    const int32_t j = 4 * (q0[u] + k);
+                    const int32_t m4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (j + c >= b0[u] && j + c < b1[u] && m4[c] != n) add(m4[c], wt[u]);
+                }
+            }
+        }
+    }
 }
 
 // Warp-cooperative validity test of pair (n, m); all lanes return the same.
@@ -154,44 +227,24 @@ k_score(ScoreArgs a) {
             for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
         }
         __syncthreads();
-        // ---- Eq. (2) accumulation ----
-        // each lane fetches one hyperedge's (omega, pin range); the warp then
-        // walks those 32 hyperedges, its lanes reading each one's pins
-        int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
-        // warp w takes hyperedges i0 + w, i0 + w + W, ... (W warps), 32 per round
-        int32_t mine = (i1 - i0 - warp_id() + kScoreWarps - 1) / kScoreWarps;
-        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
-            int32_t k = i0 + warp_id() + kScoreWarps * (r0 + lane_id());
-            int32_t we = 0, p0 = 0, p1 = 0;
-            if (r0 + lane_id() < mine) {
-                int32_t e = a.inc[k];
-                we = a.ew[e];
-                p0 = a.poff[e];
-                p1 = a.poff[e + 1];
-            }
-            int32_t cnt = min(32, mine - r0);
-            for (int32_t t = 0; t < cnt; ++t) {
-                int32_t wt = __shfl_sync(0xffffffffu, we, t);
-                int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
-                int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
-                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
-                    int32_t m = a.pins[j];
-                    if (m == n) continue;
-                    if (DENSE) {
-                        atomicAdd(&hist[m], wt);
-                    } else {
-                        uint32_t slot = hash_u32((uint32_t)m) & mask;
-                        int32_t probes = 0;
-                        for (;;) {
-                            int32_t kk = atomicCAS(&gkeys[slot], -1, m);
-                            if (kk == -1 || kk == m) { atomicAdd(&gvals[slot], wt); break; }
-                            slot = (slot + 1) & mask;
-                            if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
-                        }
-                    }
-                }
-                if (lane_id() == 0)
-                    bytes += 16ull + 4ull * (unsigned long long)(b1 - b0);  // inc, omega, 2 offsets, pins
+        // ---- Eq. (2) accumulation: warp w takes hyperedges i0 + w, i0 + w + W, ... ----
+        {
+            const int32_t i0 = a.ioff[n], deg = a.ioff[n + 1] - i0;
+            const int32_t mine = (deg - warp_id() + kScoreWarps - 1) / kScoreWarps;
+            if (DENSE) {
+                warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
+                                [&](int32_t m, int32_t wt) { atomicAdd(&hist[m], wt); }, bytes);
+            } else {
+                warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
+                                [&](int32_t m, int32_t wt) {
+                                    uint32_t slot = hash_u32((uint32_t)m) & mask;
+                                    for (int32_t probes = 0;;) {
+                                        int32_t kk = atomicCAS(&gkeys[slot], -1, m);
+                                        if (kk == -1 || kk == m) { atomicAdd(&gvals[slot], wt); break; }
+                                        slot = (slot + 1) & mask;
+                                        if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
+                                    }
+                                }, bytes);
             }
         }
         __syncthreads();

@@ -53,30 +53,15 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
             for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
         }
         // ---- Eq. (2): hyperedges of I(n) interleaved over the cluster's warps ----
-        const int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
-        const int32_t gw = rank * kScoreWarps + warp_id(), nw = kClusterCtas * kScoreWarps;
-        int32_t mine = (i1 - i0 - gw + nw - 1) / nw;
-        for (int32_t r0 = 0; r0 < mine; r0 += 32) {
-            int32_t we = 0, p0 = 0, p1 = 0;
-            if (r0 + lane_id() < mine) {
-                int32_t e = a.inc[i0 + gw + nw * (r0 + lane_id())];
-                we = a.ew[e];
-                p0 = a.poff[e];
-                p1 = a.poff[e + 1];
-            }
-            int32_t cnt = min(32, mine - r0);
-            for (int32_t t = 0; t < cnt; ++t) {
-                int32_t wt = __shfl_sync(0xffffffffu, we, t);
-                int32_t b0 = __shfl_sync(0xffffffffu, p0, t);
-                int32_t b1 = __shfl_sync(0xffffffffu, p1, t);
-                for (int32_t j = b0 + lane_id(); j < b1; j += 32) {
-                    int32_t m = a.pins[j];
-                    if (m == n) continue;
-                    int32_t owner = m / slice;
-                    atomicAdd(cl.map_shared_rank(hist, owner) + (m - owner * slice), wt);
-                }
-                if (lane_id() == 0) bytes += 16ull + 4ull * (unsigned long long)(b1 - b0);
-            }
+        {
+            const int32_t i0 = a.ioff[n], deg = a.ioff[n + 1] - i0;
+            const int32_t gw = rank * kScoreWarps + warp_id(), nw = kClusterCtas * kScoreWarps;
+            const int32_t mine = (deg - gw + nw - 1) / nw;
+            warp_accumulate(a, n, i0, gw, nw, mine,
+                            [&](int32_t m, int32_t wt) {
+                                const int32_t owner = m / slice;
+                                atomicAdd(cl.map_shared_rank(hist, owner) + (m - owner * slice), wt);
+                            }, bytes);
         }
         cl.sync();                                   // histogram complete, row(n) staged
         // ---- extraction by decreasing hist value, reduced over the cluster ----

@@ -77,6 +77,7 @@ extern "C" int hgp_score_noalloc(int32_t num_nodes, int32_t num_edges, const int
     a.pair = pair; a.score = score;
     a.status = d_max_in + 1;          // the kernel's status word (limits are never hit here)
     a.next = d_max_in + 2;            // the kernel's node counter
+    a.vec_pins = 0;                   // the caller's pins: no alignment or padding is promised
     // largest |in(n)|: union counts (and bitmaps) are needed only if 2 * max > Delta
     if (cudaMemsetAsync(d_max_in, 0, 3 * sizeof(int32_t), s) != cudaSuccess) return HGP_ERR_CUDA;
     k_noalloc_max_in<<<num_sms() * 4, 256, 0, s>>>(num_nodes, in_offsets, d_max_in);
@@ -102,7 +103,9 @@ extern "C" int hgp_score_noalloc(int32_t num_nodes, int32_t num_edges, const int
     if (allow_dynamic_smem(k_score<true>) != cudaSuccess)
         return HGP_ERR_CUDA;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, smem) !=
+        cudaSuccess)
+        return HGP_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
     int blocks = num_sms() * per_sm;
     if (blocks > num_nodes) blocks = num_nodes;

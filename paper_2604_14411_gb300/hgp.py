@@ -23,12 +23,15 @@ HGP_OK, HGP_ERR_INVALID_ARG, HGP_ERR_INFEASIBLE, HGP_ERR_OOM = 0, 1, 2, 3
 HGP_ERR_CUDA, HGP_ERR_DEVICE_LIMIT, HGP_ERR_STATE, HGP_ERR_SCRATCH_LIMIT = 4, 5, 6, 7
 HGP_INPUT_DEVICE = 1
 HGP_DELTA_INCIDENT = 4
+HGP_DELTA_OUTBOUND = 8
 HGP_OUTPUT_DEVICE = 1
 HGP_DEBUG_KEEP_LEVELS = 1
 HGP_DEBUG_TIMING = 2
 HGP_DEBUG_FORCE_GLOBAL = 4
 HGP_DEBUG_NO_BITMAP = 8
 HGP_DEBUG_FORCE_CLUSTER = 16
+HGP_DEBUG_SMALL_TABLE = 32
+HGP_DEBUG_REBUILD_INC = 64
 (HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
  HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE, HGP_LEVEL_KEY,
  HGP_LEVEL_GAIN_SEQ) = range(10)
@@ -89,6 +92,74 @@ def _options(refine_passes, debug, max_levels, model):
     return opt, cm
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class hgp_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """An hgp_allocator that draws the library's device memory from PyTorch's
+    CUDA caching allocator (torch.cuda.caching_allocator_alloc / _delete), so
+    that the library and the surrounding PyTorch program share one pool.
+
+    Keeps host-side counts for inspection: ``allocs``, ``frees``, ``live``
+    (pointer -> bytes of the chunks not yet returned), ``peak_bytes`` (the
+    most held at once).  ``fail_at`` = k > 0
+    makes the k-th allocation from now report failure (returns NULL) without
+    allocating -- a host-side fault injection for out-of-memory handling.
+    Pass the object as ``allocator=`` to Graph / hgp_create and keep it alive
+    until the handle is destroyed (Graph keeps a reference)."""
+
+    def __init__(self, device=None):
+        import threading
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.live = {}
+        self.allocs = 0
+        self.frees = 0
+        self.fail_at = 0
+        self.peak_bytes = 0
+        self._live_bytes = 0
+        self._mu = threading.Lock()
+
+        def _alloc(ctx, nbytes, stream):
+            try:
+                with self._mu:
+                    if self.fail_at > 0:
+                        self.fail_at -= 1
+                        if self.fail_at == 0:
+                            return None
+                ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+                with self._mu:
+                    self.live[int(ptr)] = int(nbytes)
+                    self.allocs += 1
+                    self._live_bytes += int(nbytes)
+                    self.peak_bytes = max(self.peak_bytes, self._live_bytes)
+                return int(ptr)
+            except Exception:       # out of memory or any other failure: report NULL
+                return None
+
+        def _free(ctx, ptr, nbytes, stream):
+            try:
+                with self._mu:
+                    self._live_bytes -= self.live.pop(int(ptr), 0)
+                    self.frees += 1
+                self._torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._c = hgp_allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+
+    @property
+    def live_bytes(self) -> int:
+        with self._mu:
+            return self._live_bytes
+
+
 class hgp_result(ctypes.Structure):
     _fields_ = [("part_ids", ctypes.c_void_p), ("part_weight", ctypes.c_void_p),
                 ("part_inbound", ctypes.c_void_p), ("out_flags", ctypes.c_uint32),
@@ -107,7 +178,7 @@ class hgp_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("moves_applied", ctypes.c_int64),
                 ("create_launches", ctypes.c_int64), ("ms_propose", ctypes.c_double),
                 ("propose_launches", ctypes.c_int64), ("propose_bytes", ctypes.c_int64),
-                ("learned_evals", ctypes.c_int64)]
+                ("learned_evals", ctypes.c_int64), ("ms_contract_kernels", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -132,7 +203,8 @@ def load(path: str = LIB_PATH):
         raise ImportError(f"libhgp.so not built at {path}; run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
     vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
-    lib.hgp_create.argtypes = [i32, i32, vp, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.hgp_create.argtypes = [i32, i32, vp, vp, vp, vp, u32, ctypes.POINTER(hgp_allocator), vp,
+                               ctypes.POINTER(vp)]
     lib.hgp_create.restype = ctypes.c_int
     lib.hgp_partition.argtypes = [vp, i64, i64, ctypes.POINTER(hgp_options), ctypes.POINTER(hgp_result)]
     lib.hgp_partition.restype = ctypes.c_int
@@ -195,10 +267,12 @@ def _check(rc, handle=None):
 
 
 def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None,
-               incident=False):
+               incident=False, allocator=None, outbound=False):
     """hgp_create: returns an opaque handle.  Arrays are all host numpy int32 or
     all torch int32 CUDA tensors.  incident=True: Delta counts every incident
-    hyperedge (HGP_DELTA_INCIDENT)."""
+    hyperedge (HGP_DELTA_INCIDENT); outbound=True: the hyperedges sourced in
+    the part (HGP_DELTA_OUTBOUND).  allocator: a TorchAllocator (or None for
+    the library's cudaMallocAsync); it must outlive the handle."""
     lib = load()
     dev = _is_device(offsets)
     arrs = [offsets, pins, node_weights, edge_weights]
@@ -210,9 +284,11 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
                 raise TypeError("device inputs must be contiguous torch.int32 CUDA tensors")
     h = ctypes.c_void_p()
     E = int(arrs[0].shape[0]) - 1
-    flags = (HGP_INPUT_DEVICE if dev else 0) | (HGP_DELTA_INCIDENT if incident else 0)
+    flags = ((HGP_INPUT_DEVICE if dev else 0) | (HGP_DELTA_INCIDENT if incident else 0) |
+             (HGP_DELTA_OUTBOUND if outbound else 0))
+    c_alloc = ctypes.byref(allocator._c) if allocator is not None else None
     rc = lib.hgp_create(int(num_nodes), E, *[_ptr(a) for a in arrs],
-                        flags, _stream_handle(stream), ctypes.byref(h))
+                        flags, c_alloc, _stream_handle(stream), ctypes.byref(h))
     _check(rc, None)
     return h
 
@@ -332,13 +408,16 @@ class Graph:
     """Owning wrapper around an hgp_graph handle."""
 
     def __init__(self, num_nodes, offsets, pins, node_weights=None, edge_weights=None, stream=None,
-                 incident=False):
+                 incident=False, allocator=None, outbound=False):
         self.num_nodes = int(num_nodes)
-        self._h = hgp_create(num_nodes, offsets, pins, node_weights, edge_weights, stream, incident)
+        self._allocator = allocator          # must outlive the handle
+        self._h = hgp_create(num_nodes, offsets, pins, node_weights, edge_weights, stream, incident,
+                             allocator, outbound)
 
     @classmethod
-    def from_hypergraph(cls, g, stream=None, incident=False):
-        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream, incident)
+    def from_hypergraph(cls, g, stream=None, incident=False, allocator=None, outbound=False):
+        return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream, incident,
+                   allocator, outbound)
 
     def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)

@@ -6,6 +6,12 @@ exhaustive enumeration.  No code is shared with the oracle or the library.
 """
 from __future__ import annotations
 
+import ctypes
+import os
+import subprocess
+import tempfile
+import threading
+
 import numpy as np
 
 
@@ -86,3 +92,45 @@ def brute_opt(num_nodes, offsets, pins, omega, delta, nw=None, ew=None):
         if best is None or c < best:
             best = c
     return best, nfeas
+
+
+_C_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "brute_opt.c")
+_c_lib = None
+_c_lock = threading.Lock()
+
+
+def _brute_c():
+    """The C enumerator of brute_opt.c, compiled once per process into a
+    temporary directory (gcc, no GPU)."""
+    global _c_lib
+    with _c_lock:
+        if _c_lib is None:
+            d = tempfile.mkdtemp(prefix="hgp_brute_")
+            so = os.path.join(d, "brute_opt.so")
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _C_SRC, "-o", so])
+            lib = ctypes.CDLL(so)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            lib.brute_optimum.argtypes = [i32, i32, vp, vp, vp, vp, i64, i64, i32,
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            lib.brute_optimum.restype = ctypes.c_int
+            _c_lib = lib
+    return _c_lib
+
+
+def brute_opt_c(num_nodes, offsets, pins, omega, delta, nw=None, ew=None, incident=False,
+                outbound=False):
+    """brute_opt by the C enumerator (up to 16 nodes, 64 hyperedges): every set
+    partition visited, branches cut as soon as a part breaks a bound.  The
+    second bound counts inbound hyperedges, or every incident one
+    (incident=True), or those sourced in the part (outbound=True).
+    Returns (optimal cost or None, number of feasible partitions)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.int32) if a is not None else None
+            for a in (offsets, pins, nw, ew)]
+    best, count = ctypes.c_int64(), ctypes.c_int64()
+    rc = _brute_c().brute_optimum(int(num_nodes), len(arrs[0]) - 1,
+                                  *[a.ctypes.data if a is not None else None for a in arrs],
+                                  int(omega), int(delta), 1 if incident else 2 if outbound else 0,
+                                  ctypes.byref(best), ctypes.byref(count))
+    if rc != 0:
+        raise ValueError("brute_optimum: graph too large for the enumerator")
+    return (None if best.value < 0 else int(best.value)), int(count.value)

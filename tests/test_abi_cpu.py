@@ -60,7 +60,7 @@ def test_error_strings_without_gpu():
     assert lib.hgp_error_string(2).decode().startswith("infeasible")
     # invalid arguments are rejected on the host before any device work
     h = ctypes.c_void_p()
-    assert lib.hgp_create(0, 0, None, None, None, None, 0, None, ctypes.byref(h)) == 1
+    assert lib.hgp_create(0, 0, None, None, None, None, 0, None, None, ctypes.byref(h)) == 1
 
 
 def test_struct_layouts_match_the_header():
@@ -70,6 +70,28 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(H.hgp_options) == 32
     assert H.hgp_options.model.offset == 24
     assert ctypes.sizeof(H.hgp_train_options) == 40
+    assert ctypes.sizeof(H.hgp_allocator) == 24
+    assert H.hgp_allocator.ctx.offset == 16
+
+
+def test_create_rejects_an_incomplete_allocator_on_the_host():
+    """An hgp_allocator without both callbacks is refused before any device
+    work (so this runs without a GPU)."""
+    from paper_2604_14411_gb300 import _build
+    from paper_2604_14411_gb300 import hgp as H
+    _build.build()
+    try:
+        lib = H.load()
+    except OSError as e:
+        pytest.skip(f"cannot dlopen without the CUDA driver: {e}")
+    import numpy as np
+    off = np.array([0, 2], np.int32)
+    pins = np.array([0, 1], np.int32)
+    half = H.hgp_allocator()            # both callbacks NULL
+    h = ctypes.c_void_p()
+    rc = lib.hgp_create(2, 1, off.ctypes.data, pins.ctypes.data, None, None, 0, ctypes.byref(half),
+                        None, ctypes.byref(h))
+    assert rc == H.HGP_ERR_INVALID_ARG and not h.value
 
 
 def test_model_from_params_rounds_to_nearest_even():

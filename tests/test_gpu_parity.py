@@ -36,10 +36,10 @@ TRACE = [(H.HGP_LEVEL_PAIR, oracle.A_PAIR), (H.HGP_LEVEL_SCORE, oracle.A_SCORE),
          (H.HGP_LEVEL_RHO_IN, oracle.A_RHO_IN), (H.HGP_LEVEL_RHO_OUT, oracle.A_RHO_OUT)]
 
 
-def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False):
-    with oracle.Run.from_graph(g, incident=incident) as r:
+def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False, outbound=False):
+    with oracle.Run.from_graph(g, incident=incident, outbound=outbound) as r:
         want = r.partition(omega, delta, passes)
-        with hgp.Graph.from_hypergraph(g, incident=incident) as G:
+        with hgp.Graph.from_hypergraph(g, incident=incident, outbound=outbound) as G:
             got = G.partition(omega, delta, passes,
                               debug=(H.HGP_DEBUG_KEEP_LEVELS if trace else 0) | debug)
             assert got.num_levels == r.num_levels
@@ -123,9 +123,46 @@ def test_weighted():
 @pytest.mark.parametrize("debug", [H.HGP_DEBUG_FORCE_GLOBAL, H.HGP_DEBUG_NO_BITMAP,
                                    H.HGP_DEBUG_FORCE_GLOBAL | H.HGP_DEBUG_NO_BITMAP,
                                    H.HGP_DEBUG_FORCE_CLUSTER,
-                                   H.HGP_DEBUG_FORCE_CLUSTER | H.HGP_DEBUG_NO_BITMAP])
+                                   H.HGP_DEBUG_FORCE_CLUSTER | H.HGP_DEBUG_NO_BITMAP,
+                                   H.HGP_DEBUG_REBUILD_INC])
 def test_fallback_paths(debug):
     compare(synth.random_snn(700, 12, 8), 20, 80, debug=debug)
+
+
+@pytest.mark.parametrize("make,omega,delta,passes,incident", [
+    (lambda: synth.snn_2k(0), 128, 512, 1, False),
+    (lambda: synth.random_snn(1500, 8, 12, size_max=300), 40, 2000, 1, False),
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400, 2, False),
+    (_weighted_graph, 30, 90, 1, False),
+    (lambda: synth.random_snn(600, 10, 3), 16, 60, 1, True)])
+def test_rebuilt_incidence_levels(make, omega, delta, passes, incident):
+    """Coarse levels whose I(n) is not kept (beyond the memory budget; forced
+    here at every level) rebuild it from their pins for refinement: the
+    whole trace stays bit-exact."""
+    compare(make(), omega, delta, passes, debug=H.HGP_DEBUG_REBUILD_INC, incident=incident)
+
+
+@pytest.mark.parametrize("make,omega,delta,cut", [
+    (lambda: synth.random_snn(1200, 24, 6), 40, 300, 1),
+    (lambda: synth.random_snn(1200, 24, 6), 40, 300, 3),
+    (lambda: synth.snn_2k(0), 128, 512, 5),
+    (lambda: synth.snn_16k(0), 1024, 4096, 1)])
+def test_cut_partition_bitexact(make, omega, delta, cut):
+    """Coarsening cut after `cut` matchings (hgp_options.max_levels; the
+    oracle's bounded prefix of the method), the clusters of the last one
+    becoming the parts: identical results.  The 16k case is the bench
+    workload's CPU-baseline sample."""
+    g = make()
+    with oracle.Run.from_graph(g) as r:
+        want = r.partition(omega, delta, 1, cut)
+        assert r.num_levels == cut
+    with hgp.Graph.from_hypergraph(g) as G:
+        got = G.partition(omega, delta, max_levels=cut)
+    assert got.num_levels == cut
+    assert np.array_equal(got.part_ids, want.part_ids)
+    assert got.cost == want.cost and got.num_parts == want.num_parts
+    assert np.array_equal(got.part_weight, want.part_weight)
+    assert np.array_equal(got.part_inbound, want.part_inbound)
 
 
 def test_cluster_path_on_the_2k_snn():
@@ -289,3 +326,34 @@ def test_incident_mode_learned_and_fill():
     assert np.array_equal(got.part_ids, want.part_ids) and got.cost == want.cost
     assert np.array_equal(got.part_inbound, want.part_inbound)
     assert np.array_equal(fill.part_ids, ids) and fill.num_parts == k
+
+
+@pytest.mark.parametrize("make,omega,delta,passes", [
+    (lambda: synth.random_snn(600, 10, 3), 16, 9, 1),
+    (lambda: synth.snn_2k(0), 128, 40, 1),
+    (_weighted_graph, 30, 12, 2),
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 30, 1),
+    (lambda: synth.random_snn(1500, 8, 12, size_max=300), 40, 25, 1)])
+def test_outbound_mode_bitexact(make, omega, delta, passes):
+    """Delta counting the hyperedges sourced in a part (HGP_DELTA_OUTBOUND):
+    level by level identical to the oracle, also on the event path of large
+    hyperedges and with several passes."""
+    compare(make(), omega, delta, passes, outbound=True)
+
+
+def test_outbound_mode_learned_fill_and_rebuild():
+    g = synth.random_snn(900, 12, 5)
+    model = synth.random_model(22, 0.5, 6)
+    with oracle.Run.from_graph(g, outbound=True) as r:
+        want = r.partition_learned(20, 11, model)
+        ids, k = r.fill_baseline(20, 11)
+    with hgp.Graph.from_hypergraph(g, outbound=True) as G:
+        got = G.partition(20, 11, model=model)
+        fill = G.fill_baseline(20, 11)
+    assert np.array_equal(got.part_ids, want.part_ids) and got.cost == want.cost
+    assert np.array_equal(got.part_inbound, want.part_inbound)
+    assert np.array_equal(fill.part_ids, ids) and fill.num_parts == k
+    compare(g, 20, 11, debug=H.HGP_DEBUG_REBUILD_INC | H.HGP_DEBUG_FORCE_CLUSTER, outbound=True)
+    with pytest.raises(H.HgpError) as ei:
+        hgp.Graph.from_hypergraph(g, incident=True, outbound=True)
+    assert ei.value.code == H.HGP_ERR_INVALID_ARG

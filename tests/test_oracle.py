@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from brute import (brute_opt, conn, edges_of, feasible, in_sets, incidence,
+from brute import (brute_opt, brute_opt_c, conn, edges_of, feasible, in_sets, incidence,
                    part_stats)
 from conftest import read_golden
 
@@ -190,6 +190,118 @@ def _random_forest(V, rng):
     return pair, score
 
 
+def _forest_edges(pair, score):
+    """Undirected edges {n, pair(n)} with weight score(n); a root two-cycle
+    is one edge."""
+    edges = {}
+    for n, m in enumerate(pair.tolist()):
+        if m >= 0:
+            edges[(min(n, m), max(n, m))] = int(score[n])
+    return edges
+
+
+def _brute_max_matching(V, edges):
+    """Largest total weight over all sets of vertex-disjoint edges."""
+    items = list(edges.items())
+    best = 0
+
+    def rec(i, used, tot):
+        nonlocal best
+        if i == len(items):
+            best = max(best, tot)
+            return
+        rec(i + 1, used, tot)
+        (a, b), w = items[i]
+        if not (used >> a) & 1 and not (used >> b) & 1:
+            rec(i + 1, used | (1 << a) | (1 << b), tot + w)
+
+    rec(0, 0, 0)
+    return best
+
+
+def _matched_weight(match, edges):
+    tot = 0
+    for n, m in enumerate(match.tolist()):
+        assert match[m] == n                       # an involution
+        if m > n:
+            assert (n, m) in edges                 # along an edge of the pseudo-forest
+            tot += edges[(n, m)]
+    return tot
+
+
+def _random_pseudo_forest(V, rng):
+    """Trees hanging off root two-cycles (or lone nodes), arbitrary weights:
+    the shape of a pairing graph without the score order of Sec. III-A."""
+    pair = -np.ones(V, np.int32)
+    score = np.zeros(V, np.int32)
+    order = rng.permutation(V)
+    k = 0
+    while k + 1 < V and rng.random() < 0.7 or k == 0:
+        a, b = order[k], order[k + 1]
+        pair[a], pair[b] = b, a
+        score[a] = score[b] = rng.integers(1, 10)
+        k += 2
+    for n in order[k:]:
+        if rng.random() < 0.15:
+            continue
+        placed = [x for x in order if pair[x] >= 0]
+        pair[n] = placed[rng.integers(len(placed))]
+        score[n] = rng.integers(1, 10)
+    return pair, score
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_dp_matching_is_a_maximum_weight_matching(seed):
+    """The exact matching (oracle method 2) against brute force over every
+    set of disjoint edges, on pseudo-forests of 10 to 14 nodes."""
+    rng = np.random.default_rng(1000 + seed)
+    V = 10 + seed % 5
+    pair, score = (_random_forest if seed % 2 else _random_pseudo_forest)(V, rng)
+    edges = _forest_edges(pair, score)
+    m = oracle.match(pair, score, 2)
+    assert _matched_weight(m, edges) == _brute_max_matching(V, edges)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dp_matching_never_below_the_two_walks(seed):
+    """On real scored levels (Eq. (2) candidates of random SNNs) and on
+    larger random forests: at least the two walks' matched weight."""
+    rng = np.random.default_rng(2000 + seed)
+    if seed < 3:
+        g = synth.random_snn(400 + 200 * seed, 12, 80 + seed)
+        with oracle.Run.from_graph(g) as r:
+            pair, score = r.score0(24, 120)
+    else:
+        pair, score = _random_forest(300, rng)
+    edges = _forest_edges(pair, score)
+    w_dp = _matched_weight(oracle.match(pair, score, 2), edges)
+    w_walks = _matched_weight(oracle.match(pair, score, 0), edges)
+    assert w_dp >= w_walks
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_whole_method_with_dp_matching(seed):
+    """matching = 1 (exact matching at every level): feasible results with
+    recounted cost, never below the exhaustive optimum on <= 12 nodes; the
+    first level's matching is the DP of the first level's candidates."""
+    rng = np.random.default_rng(400 + seed)
+    N = 10 + seed % 3
+    off, pins = tiny_random(N, int(rng.integers(6, 13)), 5, 400 + seed)
+    ins = in_sets(N, off, pins)
+    omega, delta = int(rng.integers(2, 6)), max(len(x) for x in ins) + int(rng.integers(0, 3))
+    opt, _ = brute_opt_c(N, off, pins, omega, delta)
+    with oracle.Run(N, off, pins) as r:
+        res = r.partition(omega, delta, matching=1)
+        p0, s0 = r.array(0, oracle.A_PAIR), r.array(0, oracle.A_SCORE)
+        assert np.array_equal(r.array(0, oracle.A_MATCH), oracle.match(p0, s0, 2))
+    _check_result(off, pins, N, res, omega, delta)
+    assert res.cost >= opt
+    g = synth.random_snn(700, 12, 90 + seed)
+    with oracle.Run.from_graph(g) as r:
+        res = r.partition(24, 120, matching=1)
+    _check_result(g.offsets, g.pins, g.num_nodes, res, 24, 120)
+
+
 @pytest.mark.parametrize("seed", range(20))
 def test_matching_formulations_agree_on_random_forests(seed):
     rng = np.random.default_rng(seed)
@@ -336,6 +448,186 @@ def test_whole_method_vs_exhaustive(seed):
     res = r.partition(omega, delta)
     _check_result(off, pins, N, res, omega, delta)
     assert res.cost >= opt
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_c_enumerator_agrees_with_python_enumerator(seed):
+    """The C enumerator (with branch cuts) against the plain Python
+    enumeration over every set partition, weighted and unweighted, both
+    bound kinds."""
+    rng = np.random.default_rng(900 + seed)
+    N = int(rng.integers(4, 8))
+    off, pins = tiny_random(N, int(rng.integers(2, 8)), 4, 900 + seed)
+    nw = rng.integers(1, 3, size=N).astype(np.int32) if seed % 2 else None
+    ew = rng.integers(1, 4, size=len(off) - 1).astype(np.int32) if seed % 2 else None
+    omega, delta = int(rng.integers(1, 6)), int(rng.integers(0, 5))
+    assert brute_opt_c(N, off, pins, omega, delta, nw, ew) == brute_opt(N, off, pins, omega, delta, nw, ew)
+    # incident count: in(n) replaced by every hyperedge holding n
+    best, nfeas = None, 0
+    inc = [set(e for e, ed in enumerate(edges_of(off, pins)) if n in ed) for n in range(N)]
+    import brute
+    for rho in brute.set_partitions(N):
+        st = {}
+        for n in range(N):
+            w, d = st.get(rho[n], (0, set()))
+            st[rho[n]] = (w + (1 if nw is None else int(nw[n])), d | inc[n])
+        if all(w <= omega and len(d) <= delta for w, d in st.values()):
+            nfeas += 1
+            c = conn(off, pins, rho, ew)
+            best = c if best is None or c < best else best
+    assert brute_opt_c(N, off, pins, omega, delta, nw, ew, incident=True) == (best, nfeas)
+    # outbound count: every hyperedge sourced in the part
+    best, nfeas = None, 0
+    outs = [set(e for e, ed in enumerate(edges_of(off, pins)) if ed[0] == n) for n in range(N)]
+    for rho in brute.set_partitions(N):
+        st = {}
+        for n in range(N):
+            w, d = st.get(rho[n], (0, set()))
+            st[rho[n]] = (w + (1 if nw is None else int(nw[n])), d | outs[n])
+        if all(w <= omega and len(d) <= delta for w, d in st.values()):
+            nfeas += 1
+            c = conn(off, pins, rho, ew)
+            best = c if best is None or c < best else best
+    assert brute_opt_c(N, off, pins, omega, delta, nw, ew, outbound=True) == (best, nfeas)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_whole_method_vs_exhaustive_up_to_12_nodes(seed):
+    """10 to 12 nodes (Bell(12) = 4,213,597 set partitions): the oracle's
+    result is feasible, its recounted cost is never below the optimum, and a
+    partition exists exactly when every node alone fits both bounds."""
+    rng = np.random.default_rng(300 + seed)
+    N = 10 + seed % 3
+    off, pins = tiny_random(N, int(rng.integers(6, 13)), 5, 300 + seed)
+    nw = rng.integers(1, 3, size=N).astype(np.int32) if seed % 4 == 3 else None
+    ew = rng.integers(1, 4, size=len(off) - 1).astype(np.int32) if seed % 4 == 3 else None
+    ins = in_sets(N, off, pins)
+    omega = int(rng.integers(2, 6))
+    top = max(len(s) for s in ins)
+    delta = top + int(rng.integers(0, 4)) if seed % 6 != 5 else top - 1
+    single_ok = all(len(s) <= delta for s in ins) and (nw is None or int(nw.max()) <= omega)
+    opt, nfeas = brute_opt_c(N, off, pins, omega, delta, nw, ew)
+    assert (nfeas > 0) == single_ok
+    r = oracle.Run(N, off, pins, nw, ew)
+    if not single_ok:
+        with pytest.raises(oracle.OracleError) as ei:
+            r.partition(omega, delta)
+        assert ei.value.code == oracle.INFEASIBLE
+        return
+    res = r.partition(omega, delta)
+    _check_result(off, pins, N, res, omega, delta, nw, ew)
+    assert res.cost >= opt
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_incident_mode_vs_exhaustive_up_to_12_nodes(seed):
+    rng = np.random.default_rng(700 + seed)
+    N = 11 + seed % 2
+    off, pins = tiny_random(N, int(rng.integers(6, 11)), 4, 700 + seed)
+    g = synth.Hypergraph(N, off, pins)
+    omega = 4
+    delta = max(len([e for e, ed in enumerate(edges_of(off, pins)) if n in ed]) for n in range(N)) + 1
+    opt, nfeas = brute_opt_c(N, off, pins, omega, delta, incident=True)
+    assert nfeas > 0
+    with oracle.Run.from_graph(g, incident=True) as r:
+        res = r.partition(omega, delta)
+    st = _incident_stats(g, res.part_ids)
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    assert conn(off, pins, res.part_ids) == res.cost >= opt
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cut_prefix_of_the_method(seed):
+    """max_levels bounds coarsening only: a cut at or beyond the natural level
+    count changes nothing; a cut after k matchings starts refinement from the
+    clusters of the k-th matching (gamma composed down the levels), and the
+    result is feasible with its cost recounted from sets."""
+    g = synth.random_snn(500 + 200 * seed, 12, 60 + seed)
+    omega, delta = 24, 120
+    with oracle.Run.from_graph(g) as r:
+        full = r.partition(omega, delta)
+        L = r.num_levels
+        gam = [r.array(l, oracle.A_GAMMA) for l in range(L - 1)]
+        same = r.partition(omega, delta, 1, L + 3)
+        assert np.array_equal(same.part_ids, full.part_ids) and same.cost == full.cost
+        for k in (1, 2, min(4, L)):
+            res = r.partition(omega, delta, 1, k)
+            assert r.num_levels == k and r.top_is_gamma
+            top = r.array(k - 1, oracle.A_RHO_IN)
+            assert np.array_equal(top, r.array(k - 1, oracle.A_GAMMA))
+            # the levels below the cut are the uncut run's, and each one's
+            # refinement starts from the coarser result projected by gamma
+            for l in range(k - 1):
+                assert np.array_equal(r.array(l, oracle.A_GAMMA), gam[l])
+                assert np.array_equal(r.array(l, oracle.A_RHO_IN),
+                                      r.array(l + 1, oracle.A_RHO_OUT)[gam[l]])
+            _check_result(g.offsets, g.pins, g.num_nodes, res, omega, delta)
+
+
+def _outbound_stats(g, rho):
+    """{part: (weight, |{e : src(e) in part}|)} recounted with sets."""
+    st = {}
+    for n in range(g.num_nodes):
+        p = int(rho[n])
+        w, s = st.get(p, (0, set()))
+        st[p] = (w + (1 if g.node_weights is None else int(g.node_weights[n])), s)
+    for e, ed in enumerate(edges_of(g.offsets, g.pins)):
+        st[int(rho[ed[0]])][1].add(e)
+    return {p: (w, len(s)) for p, (w, s) in st.items()}
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_outbound_mode_recounts(seed):
+    """Delta over the hyperedges sourced in a part: the result is feasible
+    under that count and the reported per-part counts equal a set recount."""
+    g = synth.random_snn(400 + 100 * seed, 10, 70 + seed, size_max=20)
+    if seed == 2:
+        rng = np.random.default_rng(3)
+        g.node_weights = rng.integers(1, 3, size=g.num_nodes).astype(np.int32)
+    omega, delta = 24, 9
+    with oracle.Run.from_graph(g, outbound=True) as r:
+        res = r.partition(omega, delta)
+    st = _outbound_stats(g, res.part_ids)
+    assert sorted(st) == list(range(res.num_parts))
+    assert [st[p][1] for p in range(res.num_parts)] == res.part_inbound.tolist()
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    assert conn(g.offsets, g.pins, res.part_ids) == res.cost
+    # one hyperedge sourced per neuron: a part's outbound count is its node count
+    if g.node_weights is None:
+        assert res.part_inbound.tolist() == np.bincount(res.part_ids).tolist()
+
+
+def test_outbound_mode_equals_inbound_when_delta_never_binds():
+    g = synth.random_snn(500, 12, 8)
+    a = oracle.partition(g, 20, 10 ** 6)
+    with oracle.Run.from_graph(g, outbound=True) as r:
+        b = r.partition(20, 10 ** 6)
+    assert np.array_equal(a.part_ids, b.part_ids) and a.cost == b.cost
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_outbound_mode_vs_exhaustive_up_to_12_nodes(seed):
+    rng = np.random.default_rng(800 + seed)
+    N = 10 + seed % 3
+    off, pins = tiny_random(N, int(rng.integers(6, 13)), 4, 800 + seed)
+    g = synth.Hypergraph(N, off, pins)
+    omega = int(rng.integers(3, 6))
+    top = max(sum(1 for e in range(len(off) - 1) if pins[off[e]] == n) for n in range(N))
+    delta = top + int(rng.integers(0, 3))
+    opt, nfeas = brute_opt_c(N, off, pins, omega, delta, outbound=True)
+    assert nfeas > 0
+    with oracle.Run.from_graph(g, outbound=True) as r:
+        res = r.partition(omega, delta)
+    st = _outbound_stats(g, res.part_ids)
+    assert all(w <= omega and d <= delta for w, d in st.values())
+    assert conn(off, pins, res.part_ids) == res.cost >= opt
+    # a node sourcing more than Delta hyperedges makes the input infeasible
+    if top >= 1:
+        with oracle.Run.from_graph(g, outbound=True) as r:
+            with pytest.raises(oracle.OracleError) as ei:
+                r.partition(omega, top - 1)
+            assert ei.value.code == oracle.INFEASIBLE
+        assert brute_opt_c(N, off, pins, omega, top - 1, outbound=True) == (None, 0)
 
 
 def test_omega_one_closed_form():

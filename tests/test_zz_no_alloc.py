@@ -2,8 +2,9 @@
 device memory while they run (code inside another framework's allocator or
 memory pool, runtimes that reserved all device memory up front).  Its only
 scratch is a fixed library-owned device array, so it must give exactly the
-candidates and scores that hgp_partition computes at its first level, call
-after call, and refuse inputs whose scratch would not fit.
+first-level candidates and scores of the CPU oracle's Eq. (2) scoring with
+the Omega/Delta checks, call after call, and refuse inputs whose scratch
+would not fit.
 
 Kept in a file of its own that sorts last, so a failure here comes after
 every other test has run.
@@ -13,6 +14,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -67,9 +69,9 @@ def score_noalloc(torch, g, omega, delta):
 
 
 def reference(g, omega, delta):
-    with hgp.Graph.from_hypergraph(g) as G:
-        G.partition(omega, delta, debug=H.HGP_DEBUG_KEEP_LEVELS)
-        return G.level_array(0, H.HGP_LEVEL_PAIR), G.level_array(0, H.HGP_LEVEL_SCORE)
+    """pair(n) and score(n) of every input node, from the CPU oracle."""
+    with oracle.Run.from_graph(g) as r:
+        return r.score0(omega, delta)
 
 
 def _max_in(g):
@@ -91,7 +93,7 @@ def _cases():
 
 
 @pytest.mark.parametrize("case", range(3))
-def test_noalloc_matches_partition_first_level_twice(torch_cuda, case):
+def test_noalloc_matches_oracle_first_level_twice(torch_cuda, case):
     name, g, omega, delta = _cases()[case]
     want_pair, want_score = reference(g, omega, delta)
     for _ in range(2):          # the shared scratch keeps the previous call's bits
