@@ -183,7 +183,14 @@ typedef struct {
     int32_t max_levels;        /* > 0: stop coarsening after this many matchings, the clusters
                                   of the last one becoming the parts (as when the node target
                                   is reached); 0 = the paper's stop rule only */
-    int32_t reserved[3];       /* must be zero */
+    int32_t matching;          /* 0: the paper's two walks over the pairing pseudo-forest
+                                  (Sec. III-B.3); 1: the exact maximum-weight matching of the
+                                  same pseudo-forest (edge {n, pair(n)} weighs score(n)), by a
+                                  tree DP -- the alternative the paper names as future work
+                                  (Sec. III-A, VI).  Ties: a node matches its best child only
+                                  for a positive gain; equal gains go to the larger id.  Plain
+                                  order only (model must be NULL) */
+    int32_t reserved[2];       /* must be zero */
     const hgp_model *model;    /* NULL: the paper's Eq. (2) order; else the learned order
                                   (host memory, read during the call) */
 } hgp_options;
@@ -205,7 +212,7 @@ typedef struct {
  * inbound-hyperedge bound `delta` (>= 0).  Parts are the non-empty clusters
  * of the final partition, renumbered 0..num_parts-1 in the order of their
  * internal ids.  The result is a pure function of (graph and its creation
- * flags, omega, delta, refine_passes, max_levels, model).
+ * flags, omega, delta, refine_passes, max_levels, matching, model).
  * Returns HGP_ERR_INFEASIBLE when some node alone has weight > omega or
  * |in(n)| > delta (then no partition exists), HGP_ERR_INVALID_ARG for bad
  * bounds/options/null part_ids.  Host outputs are complete on return; device

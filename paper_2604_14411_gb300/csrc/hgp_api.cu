@@ -28,7 +28,7 @@ cudaError_t run_fill_baseline(Arena &ar, const Level &L0, int64_t omega, int64_t
                               int32_t *part, int32_t *d_nparts, cudaStream_t s);
 cudaError_t run_match(Arena &ar, int32_t V, const int32_t *pair, const int32_t *score,
                       const int32_t *key, int32_t *match, int32_t *gamma, int32_t *d_V2,
-                      int32_t *status, cudaStream_t s);
+                      int32_t *status, cudaStream_t s, bool exact);
 cudaError_t run_contract(Arena &keep, Arena &inc_ar, Arena &roll, Arena &tmp, const Level &L,
                          int32_t V2, Level &H, const int32_t *pair, const int32_t *score,
                          int32_t *status, cudaStream_t s, PropTiming *kt);
@@ -293,12 +293,16 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
     int32_t passes = 1;
     uint32_t debug = 0;
-    int32_t max_levels = 0;
+    int32_t max_levels = 0, matching = 0;
     const hgp_model *model = nullptr;
     if (opt) {
         if (opt->refine_passes < 0) return fail(g, HGP_ERR_INVALID_ARG, "refine_passes must be >= 0");
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 2; ++i)
             if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->matching < 0 || opt->matching > 1 || (opt->matching == 1 && opt->model))
+            return fail(g, HGP_ERR_INVALID_ARG,
+                        "matching must be 0 (two walks) or 1 (exact, plain order only)");
+        matching = opt->matching;
         if (opt->model && !model_valid(opt->model))
             return fail(g, HGP_ERR_INVALID_ARG, "model: key_bits must be in 0..20 and reserved zero");
         if (opt->max_levels < 0) return fail(g, HGP_ERR_INVALID_ARG, "max_levels must be >= 0");
@@ -402,7 +406,8 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
                               tm.on ? d_bytes : nullptr, debug, s), "score");
             tm.stop(0, ev_a);
             tm.start(1, &ev_a);
-            CKP(run_match(tmp, L.V, pair, score, key, L.match, L.gamma, d_V2, d_status, s), "match");
+            CKP(run_match(tmp, L.V, pair, score, key, L.match, L.gamma, d_V2, d_status, s,
+                          matching == 1), "match");
             tm.stop(1, ev_a);
             int32_t h[2];
             CKP(cudaMemcpyAsync(&h[0], d_V2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read V2");

@@ -52,8 +52,8 @@ class hgp_model(ctypes.Structure):
 
 class hgp_options(ctypes.Structure):
     _fields_ = [("refine_passes", ctypes.c_int32), ("debug", ctypes.c_uint32),
-                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
-                ("model", ctypes.POINTER(hgp_model))]
+                ("max_levels", ctypes.c_int32), ("matching", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2), ("model", ctypes.POINTER(hgp_model))]
 
 
 class hgp_train_options(ctypes.Structure):
@@ -84,8 +84,8 @@ def _c_model(model):
     return m
 
 
-def _options(refine_passes, debug, max_levels, model):
-    opt = hgp_options(refine_passes, debug, max_levels)
+def _options(refine_passes, debug, max_levels, model, matching=0):
+    opt = hgp_options(refine_passes, debug, max_levels, matching)
     cm = _c_model(model)
     if cm is not None:
         opt.model = ctypes.pointer(cm)
@@ -294,11 +294,12 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
 
 
 def hgp_partition(handle, omega, delta, part_ids, part_weight=None, part_inbound=None,
-                  refine_passes=1, debug=0, max_levels=0, model=None):
+                  refine_passes=1, debug=0, max_levels=0, model=None, matching=0):
     """hgp_partition into caller buffers (host numpy or device torch tensors).
+    matching=1: the exact maximum-weight matching instead of the two walks.
     Returns (cost, num_parts, num_levels)."""
     lib = load()
-    opt, _keep = _options(refine_passes, debug, max_levels, model)
+    opt, _keep = _options(refine_passes, debug, max_levels, model, matching)
     res = hgp_result()
     res.part_ids = _ptr(part_ids)
     res.part_weight = _ptr(part_weight)
@@ -338,7 +339,8 @@ def hgp_destroy(handle):
         load().hgp_destroy(handle)
 
 
-def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_levels=0, model=None):
+def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_levels=0, model=None,
+                        matching=0):
     """Partitions several Graph objects concurrently; returns a list of Result."""
     lib = load()
     n = len(graphs)
@@ -355,7 +357,7 @@ def hgp_partition_batch(graphs, omegas, deltas, refine_passes=1, debug=0, max_le
         res[i].part_ids, res[i].part_weight, res[i].part_inbound = ids.ctypes.data, pw.ctypes.data, pin.ctypes.data
         res[i].out_flags = 0
     status = np.zeros(max(n, 1), dtype=np.int32)
-    opt, _keep = _options(refine_passes, debug, max_levels, model)
+    opt, _keep = _options(refine_passes, debug, max_levels, model, matching)
     rc = lib.hgp_partition_batch(handles, n, om.ctypes.data, de.ctypes.data, ctypes.byref(opt),
                                  ctypes.addressof(res), status.ctypes.data)
     if rc != HGP_OK:
@@ -419,12 +421,13 @@ class Graph:
         return cls(g.num_nodes, g.offsets, g.pins, g.node_weights, g.edge_weights, stream, incident,
                    allocator, outbound)
 
-    def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None) -> Result:
+    def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None,
+                  matching=0) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)
         pw = np.empty(self.num_nodes, dtype=np.int64)
         pin = np.empty(self.num_nodes, dtype=np.int32)
         cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug,
-                                          max_levels, model)
+                                          max_levels, model, matching)
         return Result(ids, cost, npart, nlev, pw[:npart], pin[:npart])
 
     def partition_device(self, omega, delta, part_ids, part_weight=None, part_inbound=None,

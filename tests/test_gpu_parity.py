@@ -36,12 +36,14 @@ TRACE = [(H.HGP_LEVEL_PAIR, oracle.A_PAIR), (H.HGP_LEVEL_SCORE, oracle.A_SCORE),
          (H.HGP_LEVEL_RHO_IN, oracle.A_RHO_IN), (H.HGP_LEVEL_RHO_OUT, oracle.A_RHO_OUT)]
 
 
-def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False, outbound=False):
+def compare(g, omega, delta, passes=1, debug=0, trace=True, incident=False, outbound=False,
+            matching=0):
     with oracle.Run.from_graph(g, incident=incident, outbound=outbound) as r:
-        want = r.partition(omega, delta, passes)
+        want = r.partition(omega, delta, passes, matching=matching)
         with hgp.Graph.from_hypergraph(g, incident=incident, outbound=outbound) as G:
             got = G.partition(omega, delta, passes,
-                              debug=(H.HGP_DEBUG_KEEP_LEVELS if trace else 0) | debug)
+                              debug=(H.HGP_DEBUG_KEEP_LEVELS if trace else 0) | debug,
+                              matching=matching)
             assert got.num_levels == r.num_levels
             if trace:
                 for l in range(r.num_levels):
@@ -357,3 +359,46 @@ def test_outbound_mode_learned_fill_and_rebuild():
     with pytest.raises(H.HgpError) as ei:
         hgp.Graph.from_hypergraph(g, incident=True, outbound=True)
     assert ei.value.code == H.HGP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("make,omega,delta,kw", [
+    (lambda: synth.random_snn(300, 9, 3), 10, 40, {}),
+    (lambda: synth.random_snn(1200, 24, 6), 40, 300, {}),
+    (lambda: synth.snn_2k(0), 128, 512, {}),
+    (_weighted_graph, 30, 90, {}),
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400, {"debug": H.HGP_DEBUG_FORCE_CLUSTER}),
+    (lambda: synth.random_snn(600, 10, 3), 16, 9, {"outbound": True}),
+    (lambda: synth.random_snn(800, 10, 9), 24, 100, {"passes": 3})])
+def test_exact_matching_bitexact(make, omega, delta, kw):
+    """matching = 1: the exact maximum-weight matching of every level's
+    pairing pseudo-forest (tree DP), identical level by level to the
+    oracle's DP."""
+    compare(make(), omega, delta, matching=1, **kw)
+
+
+def test_exact_matching_on_the_16k_workload_and_its_weight():
+    """The bench workload at full size: the GPU's DP matching equals the
+    oracle's DP on the first level's candidates, and it never matches less
+    score than the two walks."""
+    g = synth.snn_16k(0)
+    with hgp.Graph.from_hypergraph(g) as G:
+        G.partition(1024, 4096, debug=H.HGP_DEBUG_KEEP_LEVELS, max_levels=1, matching=1)
+        pair = G.level_array(0, H.HGP_LEVEL_PAIR).astype(np.int32)
+        score = G.level_array(0, H.HGP_LEVEL_SCORE).astype(np.int32)
+        got = G.level_array(0, H.HGP_LEVEL_MATCH).astype(np.int32)
+    with oracle.Run.from_graph(g) as r:
+        p0, s0 = r.score0(1024, 4096)
+    assert np.array_equal(pair, p0) and np.array_equal(score, s0)
+    assert np.array_equal(got, oracle.match(pair, score, 2))
+    walks = oracle.match(pair, score, 0)
+    w = lambda m: int(sum(score[n] for n in range(len(m)) if m[n] > n and pair[n] == m[n]) +
+                      sum(score[m[n]] for n in range(len(m)) if m[n] > n and pair[n] != m[n]))
+    assert w(got) >= w(walks)
+
+
+def test_exact_matching_rejects_a_model():
+    g = synth.random_snn(200, 8, 1)
+    with hgp.Graph.from_hypergraph(g) as G:
+        with pytest.raises(H.HgpError) as ei:
+            G.partition(10, 60, matching=1, model=synth.random_model(1, 0.5, 6))
+        assert ei.value.code == H.HGP_ERR_INVALID_ARG
