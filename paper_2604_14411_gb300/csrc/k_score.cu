@@ -7,8 +7,84 @@ namespace hgp {
 
 bool launch_score_cluster(const ScoreArgs &a, int max_smem, cudaStream_t s, cudaError_t *err);
 
-constexpr int64_t kBitmapBudget = 1ll << 30;   // bytes of in() bitmaps per level
+// bytes of in() bitmaps per level: a tenth of the free device memory, at
+// most 16 GiB (a popcount over two rows is far cheaper than searching sorted
+// in() lists once unions grow to thousands of hyperedges)
+static int64_t bitmap_budget() {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 1ll << 30;
+    int64_t b = (int64_t)(fr / 10);
+    return b < (16ll << 30) ? b : (16ll << 30);
+}
 constexpr int32_t kBitmapMaxWords = 8192;       // 32 KB row in shared memory
+
+// ---- per-node work buckets for levels too large for one CTA's histogram ----
+// A node whose neighbour ids all lie in a window of at most wcap ids (as in
+// layered graphs, where neighbours are spatially close) is scored by one CTA
+// with a dense histogram over that window; the others by the 8-CTA cluster
+// (or the hash tables).  The window is the span of the pin ids of I(n).
+
+// smallest and largest pin id of every hyperedge (warp per hyperedge)
+static __global__ void k_edge_span(int32_t E, const int32_t *poff, const int32_t *pins,
+                                   int32_t *emin, int32_t *emax) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = gw; e < E; e += nw) {
+        int32_t lo = 0x7fffffff, hi = -1;
+        for (int32_t j = poff[e] + lane_id(); j < poff[e + 1]; j += 32) {
+            const int32_t m = pins[j];
+            lo = min(lo, m);
+            hi = max(hi, m);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane_id() == 0) { emin[e] = lo; emax[e] = hi; }
+    }
+}
+
+// window of every node and its bucket (fit = 1: one CTA over the window;
+// nodes known to have no candidate go there too, they are answered at once)
+static __global__ void k_node_window(int32_t V, const int32_t *ioff, const int32_t *inc,
+                                     const int32_t *emin, const int32_t *emax, const uint8_t *dead,
+                                     int32_t wcap, int32_t *wlo, int32_t *whi, int32_t *fit,
+                                     int32_t *nofit) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        int32_t lo = 0x7fffffff, hi = -1;
+        for (int32_t k = ioff[n] + lane_id(); k < ioff[n + 1]; k += 32) {
+            const int32_t e = inc[k];
+            lo = min(lo, emin[e]);
+            hi = max(hi, emax[e]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane_id() == 0) {
+            if (hi < lo) { lo = 0; hi = -1; }            // no hyperedge: an empty window
+            wlo[n] = lo;
+            whi[n] = hi;
+            const int f = (dead && dead[n]) || (int64_t)hi - lo + 1 <= wcap;
+            fit[n] = f;
+            nofit[n] = 1 - f;
+        }
+    }
+}
+
+static __global__ void k_bucket_lists(int32_t V, const int32_t *fit, const int32_t *rank_fit,
+                                      const int32_t *rank_nofit, int32_t *list_fit,
+                                      int32_t *list_nofit) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (fit[i]) list_fit[rank_fit[i]] = (int32_t)i;
+        else list_nofit[rank_nofit[i]] = (int32_t)i;
+    }
+}
 
 cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
                       int32_t *pair, int32_t *score, int32_t *status,
@@ -33,7 +109,7 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     int32_t words = ((L.E + 31) / 32 + 3) & ~3;
     bool need_union = 2 * (int64_t)L.max_in > delta;
     if (need_union && !(debug & HGP_DEBUG_NO_BITMAP) && words <= kBitmapMaxWords &&
-        (int64_t)L.V * words * 4 <= kBitmapBudget) {
+        (int64_t)L.V * words * 4 <= bitmap_budget()) {
         uint32_t *bm = nullptr;
         e = dalloc(ar, &bm, (size_t)L.V * words);
         if (e) return e;
@@ -49,8 +125,69 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     size_t row_bytes = sizeof(uint32_t) * (size_t)a.bm_words;
     size_t dense_smem = row_bytes + sizeof(int32_t) * (size_t)L.V;
     bool dense = dense_smem + 2048 <= (size_t)max_smem &&
-                 !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER));
+                 !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER | HGP_DEBUG_FORCE_WINDOW));
     int sms = num_sms();
+    int64_t wcap = ((int64_t)max_smem - 2048 - (int64_t)row_bytes) / 4;
+    if (debug & HGP_DEBUG_FORCE_WINDOW) {   // test knob: small windows, so both buckets are used
+        int64_t small = L.V / 4 > 64 ? L.V / 4 : 64;
+        if (small < wcap) wcap = small;
+    }
+    if (!dense && wcap >= 64 && !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER))) {
+        int32_t *emin, *emax, *wlo, *whi, *fit, *nofit, *rfit, *rnofit, *lfit, *lnofit, *cnt;
+        e = dalloc(ar, &emin, L.E);
+        if (!e) e = dalloc(ar, &emax, L.E);
+        if (!e) e = dalloc(ar, &wlo, L.V);
+        if (!e) e = dalloc(ar, &whi, L.V);
+        if (!e) e = dalloc(ar, &fit, L.V);
+        if (!e) e = dalloc(ar, &nofit, L.V);
+        if (!e) e = dalloc(ar, &rfit, L.V);
+        if (!e) e = dalloc(ar, &rnofit, L.V);
+        if (!e) e = dalloc(ar, &lfit, L.V);
+        if (!e) e = dalloc(ar, &lnofit, L.V);
+        if (!e) e = dalloc(ar, &cnt, 3);
+        if (e) return e;
+        int wb = div_up((int64_t)(L.E > L.V ? L.E : L.V) * 32, 256);
+        if (wb > sms * 16) wb = sms * 16;
+        if (wb < 1) wb = 1;
+        if (L.E > 0) {
+            k_edge_span<<<wb, 256, 0, s>>>(L.E, L.poff, L.pins, emin, emax);
+            count_launch();
+        }
+        k_node_window<<<wb, 256, 0, s>>>(L.V, L.ioff, L.inc, emin, emax, L.dead, (int32_t)wcap, wlo,
+                                         whi, fit, nofit);
+        count_launch();
+        e = exclusive_scan_i32(ar, fit, rfit, L.V, cnt, s);
+        if (!e) e = exclusive_scan_i32(ar, nofit, rnofit, L.V, cnt + 1, s);
+        if (e) return e;
+        k_bucket_lists<<<div_up(L.V, 256) < sms * 8 ? div_up(L.V, 256) : sms * 8, 256, 0, s>>>(
+            L.V, fit, rfit, rnofit, lfit, lnofit);
+        count_launch();
+        // bucket 1: one CTA per node over its window
+        ScoreArgs w = a;
+        w.nodes = lfit;
+        w.count = cnt;
+        w.wlo = wlo;
+        w.whi = whi;
+        size_t wsmem = row_bytes + sizeof(int32_t) * (size_t)wcap;
+        e = allow_dynamic_smem(k_score<true>);
+        if (e) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads, wsmem);
+        if (e) return e;
+        if (per_sm < 1) per_sm = 1;
+        int blocks = sms * per_sm;
+        if (blocks > L.V) blocks = L.V;
+        k_score<true><<<blocks, kScoreThreads, wsmem, s>>>(w);
+        count_launch();
+        e = cudaGetLastError();
+        if (e) return e;
+        // bucket 2: the rest, on the cluster (or the hash tables below)
+        a.nodes = lnofit;
+        a.count = cnt + 1;
+        e = dalloc(ar, &a.next, 1);
+        if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
+        if (e) return e;
+    }
     if (dense) {
         e = allow_dynamic_smem(k_score<true>);
         if (e) return e;

@@ -50,6 +50,11 @@ struct ScoreArgs {
     int32_t *next;                   // work counter: nodes are taken dynamically
     int32_t vec_pins;                // pins readable as 16-byte vectors: 16-byte aligned, and
                                      // the allocation extends to a multiple of 16 bytes
+    // per-node work lists (null: every node 0..V-1): nodes[0 .. *count)
+    const int32_t *nodes, *count;
+    // dense mode, windowed: node n's neighbours all lie in [wlo[n], whi[n]] and
+    // its histogram holds only that window (null: the whole id range)
+    const int32_t *wlo, *whi;
 };
 
 // m is worth checking for n: alive, and either newly merged or ranked below
@@ -86,8 +91,9 @@ __device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
 // 16-byte slice of each before any of its adds, so a warp keeps up to 2 KB
 // of pin loads in flight instead of one 128-byte load per hyperedge (the
 // loop is otherwise bound by load latency).  Slices are aligned to 4 pins
-// and masked to the hyperedge's range.  With vec_pins = 0 pins are read one
-// per lane.
+// and masked to the hyperedge's range; warp shuffles then give each add
+// instruction 32 consecutive pins.  With vec_pins = 0 pins are read one per
+// lane.
 constexpr int kAccEdges = 4;
 
 template <typename Add>
@@ -132,22 +138,52 @@ __device__ __forceinline__ void warp_accumulate(const ScoreArgs &a, int32_t n, i
                 span = max(span, ((b1[u] + 3) >> 2) - q0[u]);
                 if (lane == 0) bytes += t + u < cnt ? 16ull + 4ull * (unsigned long long)(b1[u] - b0[u]) : 0ull;
             }
-            for (int32_t k = lane; k < span; k += 32) {
+            for (int32_t kb = 0; kb < span; kb += 32) {
+                // lane l loads pins 4 (q0 + kb + l) .. + 3 of every hyperedge ...
                 int4 v[kAccEdges];
 #pragma unroll
                 for (int u = 0; u < kAccEdges; ++u)
-                    v[u] = 4 * (q0[u] + k) < b1[u] ? pv[q0[u] + k] : make_int4(-1, -1, -1, -1);
+                    v[u] = 4 * (q0[u] + kb + lane) < b1[u] ? pv[q0[u] + kb + lane] : make_int4(-1, -1, -1, -1);
+                // ... and the warp's 128 pins are handed out so that step c gives
+                // lane l pin 32 c + l: each add instruction then covers 32
+                // consecutive pins, as a scalar walk would (consecutive ids --
+                // sorted targets -- then fall in distinct banks, and in one
+                // remote CTA's slice on the cluster)
 #pragma unroll
                 for (int u = 0; u < kAccEdges; ++u) {
-                    const int32_t j = 4 * (q0[u] + k);
-                    const int32_t m4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                    const int32_t j0 = 4 * (q0[u] + kb);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (j + c >= b0[u] && j + c < b1[u] && m4[c] != n) add(m4[c], wt[u]);
+                    for (int c = 0; c < 4; ++c) {
+                        const int from = 8 * c + (lane >> 2);
+                        const int32_t x = __shfl_sync(0xffffffffu, v[u].x, from);
+                        const int32_t y = __shfl_sync(0xffffffffu, v[u].y, from);
+                        const int32_t z = __shfl_sync(0xffffffffu, v[u].z, from);
+                        const int32_t w = __shfl_sync(0xffffffffu, v[u].w, from);
+                        const int sel = lane & 3;
+                        const int32_t m = sel == 0 ? x : sel == 1 ? y : sel == 2 ? z : w;
+                        const int32_t j = j0 + 32 * c + lane;
+                        if (j >= b0[u] && j < b1[u] && m != n) add(m, wt[u]);
+                    }
                 }
             }
         }
     }
+}
+
+// CTA-wide maxima of two values at once (red: 2 * kScoreWarps entries).
+__device__ __forceinline__ void block_max2_i32(int32_t &x, int32_t &y, int32_t *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
+    }
+    __syncthreads();
+    if (lane_id() == 0) { red[warp_id()] = x; red[kScoreWarps + warp_id()] = y; }
+    __syncthreads();
+    x = red[0];
+    y = red[kScoreWarps];
+#pragma unroll
+    for (int i = 1; i < kScoreWarps; ++i) { x = max(x, red[i]); y = max(y, red[kScoreWarps + i]); }
 }
 
 // Warp-cooperative validity test of pair (n, m); all lanes return the same.
@@ -196,26 +232,30 @@ k_score(ScoreArgs a) {
     // layout: [row of in(n): bm_words][dense hist V]
     uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
     int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
-    __shared__ int32_t red[kScoreWarps];
+    __shared__ int32_t red[2 * kScoreWarps];
 
     int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
     int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
-    const int32_t cap = DENSE ? a.V : a.gcap;
     const uint32_t mask = (uint32_t)a.gcap - 1u;
     unsigned long long bytes = 0;
 
     __shared__ int32_t s_n;
+    const int32_t count = a.nodes ? *a.count : a.V;
     for (;;) {
         if (threadIdx.x == 0) s_n = atomicAdd(a.next, 1);
         __syncthreads();
-        const int32_t n = s_n;
-        if (n >= a.V) break;
+        const int32_t t = s_n;
+        if (t >= count) break;
+        const int32_t n = a.nodes ? a.nodes[t] : t;
         if (a.dead && a.dead[n]) {              // no valid candidate can exist
             if (threadIdx.x == 0) { a.pair[n] = -1; a.score[n] = 0; }
             __syncthreads();
             continue;
         }
         const unsigned long long thr = a.thr ? a.thr[n] : 0ull;
+        // dense table: ids base .. base + cap - 1 (the node's window, or all)
+        const int32_t base = (DENSE && a.wlo) ? a.wlo[n] : 0;
+        const int32_t cap = DENSE ? (a.wlo ? max(0, a.whi[n] - base + 1) : a.V) : a.gcap;
         // ---- clear; stage row(n) ----
         for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
             if (DENSE) hist[i] = 0;
@@ -233,7 +273,7 @@ k_score(ScoreArgs a) {
             const int32_t mine = (deg - warp_id() + kScoreWarps - 1) / kScoreWarps;
             if (DENSE) {
                 warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
-                                [&](int32_t m, int32_t wt) { atomicAdd(&hist[m], wt); }, bytes);
+                                [&](int32_t m, int32_t wt) { atomicAdd(&hist[m - base], wt); }, bytes);
             } else {
                 warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
                                 [&](int32_t m, int32_t wt) {
@@ -249,38 +289,53 @@ k_score(ScoreArgs a) {
         }
         __syncthreads();
         // ---- extraction by decreasing hist value ----
-        int64_t in_n = a.noff[n + 1] - a.noff[n];
-        int32_t hcur = 0x7fffffff, result = -1, rscore = 0;
-        for (;;) {
-            int32_t hm = 0;
-            for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
-                int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
-                if (h < hcur && h > hm && eligible(a, DENSE ? i : gkeys[i], h, thr)) hm = h;
+        // Which neighbours may be the candidate does not change during the
+        // extraction (eligible() depends on m and hist(n, m) only), so the
+        // others are cleared from the table once; every round then scans the
+        // table in shared memory alone, checking the tie group of value hmax
+        // and finding the next lower value in the same pass.
+        int32_t hmax = 0;
+        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+            const int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
+            if (h <= 0) continue;
+            if (!eligible(a, DENSE ? base + i : gkeys[i], h, thr)) {
+                if (DENSE) hist[i] = 0; else gvals[i] = 0;
+            } else {
+                hmax = max(hmax, h);
             }
-            int32_t hmax = block_max_i32(hm, red);
-            if (hmax == 0) break;
-            // every neighbour with hist == hmax, one warp per candidate
-            int32_t best_id = -1;
-            int32_t per_warp = (((cap + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
-            int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
+        }
+        hmax = block_max_i32(hmax, red);
+        const int64_t in_n = a.noff[n + 1] - a.noff[n];
+        int32_t result = -1, rscore = 0;
+        const int32_t per_warp = (((cap + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+        const int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
+        while (hmax > 0) {
+            // every neighbour with hist == hmax, one warp per candidate; nxt =
+            // the largest value below hmax (complete whenever no warp found a
+            // valid candidate, since only a find ends a warp's scan early)
+            int32_t best_id = -1, nxt = 0;
             if (DENSE) {
                 // ids are table indices: scan downwards, the first valid is this warp's best
-                for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
-                    int32_t i = base + lane_id();
-                    bool hit = i < hi && hist[i] == hmax && eligible(a, i, hmax, thr);
-                    unsigned ball = __ballot_sync(0xffffffffu, hit);
+                for (int32_t b0 = lo + ((hi - lo - 1) & ~31); b0 >= lo && best_id < 0; b0 -= 32) {
+                    const int32_t i = b0 + lane_id();
+                    const int32_t h = i < hi ? hist[i] : 0;
+                    if (h < hmax) nxt = max(nxt, h);
+                    unsigned ball = __ballot_sync(0xffffffffu, h == hmax);
                     while (ball && best_id < 0) {
                         int src = 31 - __clz(ball);
                         ball &= ~(1u << src);
-                        if (warp_check(a, n, base + src, row_n, in_n, bytes)) best_id = base + src;
+                        if (warp_check(a, n, base + b0 + src, row_n, in_n, bytes)) best_id = base + b0 + src;
                     }
                 }
             } else {
-                for (int32_t base = lo; base < hi; base += 32) {
-                    int32_t i = base + lane_id();
-                    int32_t m = -1;
-                    if (i < hi && gkeys[i] >= 0 && gvals[i] == hmax && eligible(a, gkeys[i], hmax, thr))
-                        m = gkeys[i];
+                for (int32_t b0 = lo; b0 < hi; b0 += 32) {
+                    const int32_t i = b0 + lane_id();
+                    int32_t m = -1, h = 0;
+                    if (i < hi && gkeys[i] >= 0) {
+                        h = gvals[i];
+                        if (h == hmax) m = gkeys[i];
+                        else if (h < hmax) nxt = max(nxt, h);
+                    }
                     unsigned ball = __ballot_sync(0xffffffffu, m >= 0);
                     while (ball) {
                         int src = __ffs(ball) - 1;
@@ -290,9 +345,9 @@ k_score(ScoreArgs a) {
                     }
                 }
             }
-            int32_t win = block_max_i32(best_id, red);
-            if (win >= 0) { result = win; rscore = hmax; break; }
-            hcur = hmax;
+            block_max2_i32(best_id, nxt, red);
+            if (best_id >= 0) { result = best_id; rscore = hmax; break; }
+            hmax = nxt;
         }
         if (threadIdx.x == 0) {
             a.pair[n] = result;

@@ -21,19 +21,20 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
     int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
-    __shared__ int32_t red[kScoreWarps];
-    __shared__ int32_t s_node, s_xchg, s_bcast;
+    __shared__ int32_t red[2 * kScoreWarps];
+    __shared__ int32_t s_node, s_xchg[2], s_bcast[2];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int32_t id0 = rank * slice;
     const int32_t len = max(0, min(slice, a.V - id0));
     unsigned long long bytes = 0;
 
+    const int32_t count = a.nodes ? *a.count : a.V;
     for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) hist[i] = 0;
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
             int32_t t = atomicAdd(a.next, 1);
-            s_node = t < a.V ? t : a.V;
+            s_node = t < count ? (a.nodes ? a.nodes[t] : t) : a.V;
         }
         cl.sync();                                   // slices cleared, node published
         const int32_t n = *cl.map_shared_rank(&s_node, 0);
@@ -65,50 +66,59 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
         }
         cl.sync();                                   // histogram complete, row(n) staged
         // ---- extraction by decreasing hist value, reduced over the cluster ----
+        // As in k_score: ineligible neighbours are cleared from the slice once;
+        // each round checks the tie group of value hmax and finds the next lower
+        // value in the same scan, and one exchange over the cluster settles both.
+        int32_t hloc = 0;
+        for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) {
+            const int32_t h = hist[i];
+            if (h <= 0) continue;
+            if (!eligible(a, id0 + i, h, thr)) hist[i] = 0;
+            else hloc = max(hloc, h);
+        }
+        hloc = block_max_i32(hloc, red);
+        if (threadIdx.x == 0) { s_xchg[0] = -1; s_xchg[1] = hloc; }
+        cl.sync();
+        if (threadIdx.x == 0) {
+            int32_t v = 0;
+            for (int r = 0; r < kClusterCtas; ++r) v = max(v, cl.map_shared_rank(s_xchg, r)[1]);
+            s_bcast[1] = v;
+        }
+        cl.sync();                                   // all reads of s_xchg done
+        int32_t hmax = s_bcast[1];
         const int64_t in_n = a.noff[n + 1] - a.noff[n];
-        int32_t hcur = 0x7fffffff, result = -1, rscore = 0;
-        for (;;) {
-            int32_t hm = 0;
-            for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) {
-                int32_t h = hist[i];
-                if (h < hcur && h > hm && eligible(a, id0 + i, h, thr)) hm = h;
-            }
-            hm = block_max_i32(hm, red);
-            if (threadIdx.x == 0) s_xchg = hm;
-            cl.sync();
-            if (threadIdx.x == 0) {
-                int32_t v = 0;
-                for (int r = 0; r < kClusterCtas; ++r) v = max(v, *cl.map_shared_rank(&s_xchg, r));
-                s_bcast = v;
-            }
-            cl.sync();                               // all reads of s_xchg done
-            const int32_t hmax = s_bcast;
-            if (hmax == 0) break;
-            int32_t best_id = -1;
-            int32_t per_warp = (((len + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
-            int32_t lo = warp_id() * per_warp, hi = min(len, lo + per_warp);
+        int32_t result = -1, rscore = 0;
+        const int32_t per_warp = (((len + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+        const int32_t lo = warp_id() * per_warp, hi = min(len, lo + per_warp);
+        while (hmax > 0) {
+            int32_t best_id = -1, nxt = 0;
             for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
-                int32_t i = base + lane_id();
-                bool hit = i < hi && hist[i] == hmax && eligible(a, id0 + i, hmax, thr);
-                unsigned ball = __ballot_sync(0xffffffffu, hit);
+                const int32_t i = base + lane_id();
+                const int32_t h = i < hi ? hist[i] : 0;
+                if (h < hmax) nxt = max(nxt, h);
+                unsigned ball = __ballot_sync(0xffffffffu, h == hmax);
                 while (ball && best_id < 0) {
                     int src = 31 - __clz(ball);
                     ball &= ~(1u << src);
                     if (warp_check(a, n, id0 + base + src, row_n, in_n, bytes)) best_id = id0 + base + src;
                 }
             }
-            best_id = block_max_i32(best_id, red);
-            if (threadIdx.x == 0) s_xchg = best_id;
+            block_max2_i32(best_id, nxt, red);
+            if (threadIdx.x == 0) { s_xchg[0] = best_id; s_xchg[1] = nxt; }
             cl.sync();
             if (threadIdx.x == 0) {
-                int32_t v = -1;
-                for (int r = 0; r < kClusterCtas; ++r) v = max(v, *cl.map_shared_rank(&s_xchg, r));
-                s_bcast = v;
+                int32_t b = -1, x = 0;
+                for (int r = 0; r < kClusterCtas; ++r) {
+                    const int32_t *o = cl.map_shared_rank(s_xchg, r);
+                    b = max(b, o[0]);
+                    x = max(x, o[1]);
+                }
+                s_bcast[0] = b;
+                s_bcast[1] = x;
             }
             cl.sync();
-            const int32_t win = s_bcast;
-            if (win >= 0) { result = win; rscore = hmax; break; }
-            hcur = hmax;
+            if (s_bcast[0] >= 0) { result = s_bcast[0]; rscore = hmax; break; }
+            hmax = s_bcast[1];
         }
         if (rank == 0 && threadIdx.x == 0) {
             a.pair[n] = result;

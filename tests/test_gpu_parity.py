@@ -126,9 +126,21 @@ def test_weighted():
                                    H.HGP_DEBUG_FORCE_GLOBAL | H.HGP_DEBUG_NO_BITMAP,
                                    H.HGP_DEBUG_FORCE_CLUSTER,
                                    H.HGP_DEBUG_FORCE_CLUSTER | H.HGP_DEBUG_NO_BITMAP,
-                                   H.HGP_DEBUG_REBUILD_INC])
+                                   H.HGP_DEBUG_REBUILD_INC, H.HGP_DEBUG_FORCE_WINDOW,
+                                   H.HGP_DEBUG_FORCE_WINDOW | H.HGP_DEBUG_NO_BITMAP])
 def test_fallback_paths(debug):
     compare(synth.random_snn(700, 12, 8), 20, 80, debug=debug)
+
+
+@pytest.mark.parametrize("make,omega,delta", [
+    (lambda: synth.conv_snn(4, 6, 8, 5, 8, 3), 48, 400),
+    (lambda: synth.conv_snn(6, 8, 8, 6, 12, 5), 64, 300),
+    (lambda: synth.snn_2k(0), 128, 512)])
+def test_window_buckets(make, omega, delta):
+    """Per-node buckets (the path of levels too large for one CTA): nodes
+    whose neighbour ids fit a small window get one CTA over that window, the
+    rest the 8-CTA cluster; layered graphs put many nodes in each bucket."""
+    compare(make(), omega, delta, debug=H.HGP_DEBUG_FORCE_WINDOW)
 
 
 @pytest.mark.parametrize("make,omega,delta,passes,incident", [
