@@ -337,6 +337,22 @@ def learned_leg(args, timed, g, d_ids, plain_cost, plain_ms, H, stream):
     ms = statistics.median(times)
     ids = d_ids.cpu().numpy()
     cost, feasible = recount(g, ids, OMEGA, DELTA)
+    # the same model with the hidden layer on tensor cores (learned_eval = 1)
+    timed(model=model, learned_eval=1)
+    truns = [timed(model=model, learned_eval=1) for _ in range(max(1, min(args.steps, 3)))]
+    tms = statistics.median(r[0] for r in truns)
+    tres = truns[-1][1]
+    tcost, tfeas = recount(g, d_ids.cpu().numpy(), OMEGA, DELTA)
+    tstats = [timed(H.HGP_DEBUG_TIMING, model=model, learned_eval=1)[2]
+              for _ in range(INSTRUMENTED_STEPS)]
+    tsc = sum(s["ms_score"] for s in tstats) / len(tstats)
+    tensor = {"learned_eval": 1, "ms_per_step": tms, "pins_per_s": g.num_pins / (tms / 1000.0),
+              "levels": tres[2], "cost": tres[0], "cost_recounted": tcost, "feasible": tfeas,
+              "cost_ratio_vs_plain": tres[0] / plain_cost, "time_ratio_vs_plain": tms / plain_ms,
+              "score_ms_per_step": tsc,
+              "note": "hidden layer by mma.sync m16n8k8 (TF32 in, FP32 accumulate) over each warp's "
+                      "32 queued candidates; scores agree with FP32 to ~1e-3, so the partition may "
+                      "differ from the FMA-chain order's"}
     # the learned scorer's FP32 roofline: 1,152 FLOP per network evaluation
     # (64 x 8 + 64 FMA) against 152 SMs x 128 FP32 lanes x 2 FLOP x the SM clock
     sc_ms = sum(s["ms_score"] for s in stats)
@@ -358,7 +374,7 @@ def learned_leg(args, timed, g, d_ids, plain_cost, plain_ms, H, stream):
             "levels": stats[-1]["num_levels"], "cost": res[0], "num_parts": res[1],
             "cost_recounted": cost, "feasible": feasible,
             "cost_ratio_vs_plain": res[0] / plain_cost, "time_ratio_vs_plain": ms / plain_ms,
-            "steps": len(times),
+            "steps": len(times), "tensor_cores": tensor,
             "roofline": {"kernel": "k_score_learned (network-ranked scoring)", "bound": "alu",
                          "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": None,
@@ -460,6 +476,26 @@ def run_learned_large(args, rank, world):
         dist.destroy_process_group()
 
 
+def profile_large(levels):
+    """One plain partition of the 262k SNN cut after `levels` levels."""
+    import torch
+    import synth
+    from paper_2604_14411_gb300 import hgp as H
+    H.load()
+    g = synth.snn_256k(0)
+    dev = torch.device("cuda", 0)
+    d_off = torch.from_numpy(g.offsets.copy()).to(dev)
+    d_pins = torch.from_numpy(g.pins.copy()).to(dev)
+    d_ids = torch.empty(g.num_nodes, dtype=torch.int32, device=dev)
+    h = H.hgp_create(g.num_nodes, d_off, d_pins)
+    try:
+        res = H.hgp_partition(h, 1 << 10, 1 << 12, d_ids, None, None, 1, 0, levels)
+    finally:
+        H.hgp_destroy(h)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_large": True, "levels": res[2], "cost": res[0], "parts": res[1]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,6 +521,9 @@ def main():
                     help="with --profile-step: profile one step with this saved model")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run exactly one step, exit (for ncu launch lists)")
+    ap.add_argument("--profile-large", type=int, default=0, metavar="LEVELS",
+                    help="one plain partition of the 262,144-node SNN cut after LEVELS "
+                         "coarsening levels, then exit (for ncu captures of its large levels)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.profile_step:
         args.warmup = 3
@@ -494,6 +533,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile_large:
+        return profile_large(args.profile_large)
     if args.workload == "batch64":
         return run_batch(args, rank, world)
     if args.workload in ("learned256k", "learnedconv200k"):
@@ -521,22 +562,23 @@ def main():
     d_pin = torch.empty(N, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
-    def step(debug=0, model=None, max_levels=0):
+    def step(debug=0, model=None, max_levels=0, learned_eval=0):
         h = H.hgp_create(N, d_off, d_pins, stream=stream)
         try:
-            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug, max_levels, model)
+            res = H.hgp_partition(h, OMEGA, DELTA, d_ids, d_pw, d_pin, 1, debug, max_levels, model,
+                                  learned_eval=learned_eval)
             st = H.hgp_get_stats(h)
         finally:
             H.hgp_destroy(h)
         return res, st
 
-    def timed(debug=0, model=None, max_levels=0):
+    def timed(debug=0, model=None, max_levels=0, learned_eval=0):
         """One step between CUDA events on the library's stream, L2 flushed first."""
         flush.fill_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        res, st = step(debug, model, max_levels)
+        res, st = step(debug, model, max_levels, learned_eval)
         b.record(stream)
         b.synchronize()
         return a.elapsed_time(b), res, st
@@ -716,8 +758,9 @@ def large_leg(model, stream, H, peak):
                        "67,108,864 pins, int32 CSR, Omega=2^10, Delta=2^12, seed 0",
            "timing": "one whole create + partition + destroy each, CUDA events on the library's "
                      "stream, L2 flushed before, phase events on"}
-    legs = [("plain", None)] + ([("learned", model)] if model is not None else [])
-    for name, m in legs:
+    legs = [("plain", None, 0)] + ([("learned", model, 0), ("learned_tensor_cores", model, 1)]
+                                   if model is not None else [])
+    for name, m, tc in legs:
         flush.fill_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -725,7 +768,8 @@ def large_leg(model, stream, H, peak):
         a.record(stream)
         h = H.hgp_create(g.num_nodes, d_off, d_pins, stream=stream, allocator=alloc)
         try:
-            res = H.hgp_partition(h, 1 << 10, 1 << 12, d_ids, None, None, 1, H.HGP_DEBUG_TIMING, 0, m)
+            res = H.hgp_partition(h, 1 << 10, 1 << 12, d_ids, None, None, 1, H.HGP_DEBUG_TIMING, 0, m,
+                                  learned_eval=tc)
             st = H.hgp_get_stats(h)
         finally:
             H.hgp_destroy(h)
@@ -740,9 +784,10 @@ def large_leg(model, stream, H, peak):
         if name == "plain":
             out["contraction_roofline"] = contraction_roofline([st], peak, load_peaks()[1],
                                                                "262k SNN, all 201 levels")
-    if "learned" in out:
-        out["learned"]["cost_ratio_vs_plain"] = out["learned"]["cost"] / out["plain"]["cost"]
-        out["learned"]["time_ratio_vs_plain"] = out["learned"]["ms"] / out["plain"]["ms"]
+    for name in ("learned", "learned_tensor_cores"):
+        if name in out:
+            out[name]["cost_ratio_vs_plain"] = out[name]["cost"] / out["plain"]["cost"]
+            out[name]["time_ratio_vs_plain"] = out[name]["ms"] / out["plain"]["ms"]
     del d_off, d_pins, d_ids, flush
     torch.cuda.empty_cache()
     return out

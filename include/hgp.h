@@ -194,7 +194,12 @@ typedef struct {
                                   (Sec. III-A, VI).  Ties: a node matches its best child only
                                   for a positive gain; equal gains go to the larger id.  Plain
                                   order only (model must be NULL) */
-    int32_t reserved[2];       /* must be zero */
+    int32_t learned_eval;      /* with a model: 0 evaluates the network as the float32 FMA
+                                  chains described above (keys reproducible bit for bit);
+                                  1 evaluates its hidden layer on tensor cores (TF32 inputs,
+                                  float32 accumulation, 32 candidates per warp-level MMA batch):
+                                  scores agree with float32 to about 1e-3, not bit for bit */
+    int32_t reserved[1];       /* must be zero */
     const hgp_model *model;    /* NULL: the paper's Eq. (2) order; else the learned order
                                   (host memory, read during the call) */
 } hgp_options;
@@ -216,7 +221,7 @@ typedef struct {
  * inbound-hyperedge bound `delta` (>= 0).  Parts are the non-empty clusters
  * of the final partition, renumbered 0..num_parts-1 in the order of their
  * internal ids.  The result is a pure function of (graph and its creation
- * flags, omega, delta, refine_passes, max_levels, matching, model).
+ * flags, omega, delta, refine_passes, max_levels, matching, model, learned_eval).
  * Returns HGP_ERR_INFEASIBLE when some node alone has weight > omega or
  * |in(n)| > delta (then no partition exists), HGP_ERR_INVALID_ARG for bad
  * bounds/options/null part_ids.  Host outputs are complete on return; device

@@ -12,14 +12,14 @@
 #include "hgp_internal.cuh"
 
 namespace hgp {
-cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
-                      int32_t *pair, int32_t *score, int32_t *status,
+cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const int32_t *ew,
+                      int64_t omega, int64_t delta, int32_t *pair, int32_t *score, int32_t *status,
                       unsigned long long *bytes, uint32_t debug, cudaStream_t s);
 cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
                               int64_t delta, const hgp_model *model, int32_t *pair,
                               int32_t *score, int32_t *key, int32_t *status,
                               unsigned long long *bytes, unsigned long long *evals,
-                              uint32_t debug, cudaStream_t s);
+                              uint32_t debug, int32_t tensor_cores, cudaStream_t s);
 bool model_valid(const hgp_model *m);
 cudaError_t run_learn_samples(const Level &L0, const int32_t *ew, const int32_t *part_ids,
                               uint64_t seed, int32_t per_node, float *x, float *y,
@@ -293,12 +293,14 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
     if (!res->part_ids) return fail(g, HGP_ERR_INVALID_ARG, "part_ids is required");
     int32_t passes = 1;
     uint32_t debug = 0;
-    int32_t max_levels = 0, matching = 0;
+    int32_t max_levels = 0, matching = 0, learned_eval = 0;
     const hgp_model *model = nullptr;
     if (opt) {
         if (opt->refine_passes < 0) return fail(g, HGP_ERR_INVALID_ARG, "refine_passes must be >= 0");
-        for (int i = 0; i < 2; ++i)
-            if (opt->reserved[i]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->reserved[0]) return fail(g, HGP_ERR_INVALID_ARG, "reserved options must be zero");
+        if (opt->learned_eval < 0 || opt->learned_eval > 1 || (opt->learned_eval && !opt->model))
+            return fail(g, HGP_ERR_INVALID_ARG, "learned_eval must be 0, or 1 with a model");
+        learned_eval = opt->learned_eval;
         if (opt->matching < 0 || opt->matching > 1 || (opt->matching == 1 && opt->model))
             return fail(g, HGP_ERR_INVALID_ARG,
                         "matching must be 0 (two walks) or 1 (exact, plain order only)");
@@ -401,10 +403,11 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
             if (model)
                 CKP(run_score_learned(tmp, L, g->ew, omega, delta, model, pair, score, key, d_status,
                                       tm.on ? d_bytes : nullptr, tm.on ? d_bytes + 1 : nullptr,
-                                      debug, s), "score");
+                                      debug, learned_eval, s), "score");
             else
-                CKP(run_score(tmp, L, g->ew, omega, delta, pair, score, d_status,
-                              tm.on ? d_bytes : nullptr, debug, s), "score");
+                CKP(run_score(tmp, roll[l & 1], L, l > 0 ? &levels[l - 1] : nullptr, g->ew, omega,
+                              delta, pair, score, d_status, tm.on ? d_bytes : nullptr, debug, s),
+                    "score");
             tm.stop(0, ev_a);
             tm.start(1, &ev_a);
             CKP(run_match(tmp, L.V, pair, score, key, L.match, L.gamma, d_V2, d_status, s,
@@ -449,6 +452,7 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
                 O.dead = O.merged = nullptr;
                 O.thr = nullptr;
                 O.old_id = nullptr;
+                O.bm = nullptr;
                 if (O.inc_rolling) O.ioff = O.inc = nullptr;
             }
             const size_t inc_bytes = 4 * ((size_t)L.P + (size_t)L.V + 1) + 512;   // H.P <= L.P

@@ -57,6 +57,11 @@ struct Level {
     // I(n) lives with in(n) in storage that the next-but-one contraction
     // reuses; refinement then rebuilds it from the pins
     bool inc_rolling = false;
+    // in() bitmaps of this level's scoring (null when it used none): row n is
+    // bm[n * bm_words ..], bit e set iff e in in(n); kept with in(n), so the
+    // next level can build its rows as ORs of the matched pairs' rows
+    uint32_t *bm = nullptr;
+    int32_t bm_words = 0;
 };
 
 // ---------------- stream-ordered device memory ----------------

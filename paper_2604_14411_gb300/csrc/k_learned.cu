@@ -69,6 +69,8 @@ struct LearnedArgs {
     int32_t *gkeys, *gvals, *ginter, *gused;
     int32_t gcap;
     unsigned long long *bytes, *evals;
+    int32_t tc;                  // 1: evaluate the network on tensor cores (mlp_eval_tc)
+    const float *tcw;            // tc: W1 (512), b1 (64), W2 (64), b2 as float32, device memory
 };
 
 __device__ __forceinline__ float pow2_exact(int k) {       // 2^k, -126 <= k <= 127
@@ -93,6 +95,95 @@ __device__ __forceinline__ float mlp_eval(const MlpParams &M, const float *x) {
         s = __fmaf_rn(M.w2[j], h, s);
     }
     return s;
+}
+
+// ---- tensor-core evaluation (hgp_options.learned_eval = 1) ----
+// The warp's 32 queued candidates are two 16 x 8 tiles of features; the
+// hidden layer is those tiles times W1^T (8 x 64, eight 8-column tiles) by
+// mma.sync m16n8k8 with TF32 inputs and FP32 accumulation (16 MMAs per 32
+// candidates instead of 32 x 512 FMAs).  Bias, ReLU and the output layer are
+// applied to the accumulator fragments and summed over the four lanes that
+// hold a row.  The bfloat16 weights are exact in TF32; the features are
+// rounded to TF32 (10-bit mantissa), so scores differ from the FMA chains in
+// the last bits -- this mode is checked against a float32 reference within
+// a tolerance, not bit for bit.
+__device__ __forceinline__ uint32_t to_tf32(float f) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32_m16n8k8(float &d0, float &d1, float &d2, float &d3,
+                                                 uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                 uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                 "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float pick4(float v0, float v1, float v2, float v3, int i) {
+    return i == 0 ? v0 : i == 1 ? v1 : i == 2 ? v2 : v3;
+}
+
+// Score of lane r's candidate (row r); x = this lane's 8 features, sw = the
+// network staged in shared memory (W1 at 8 j + i, b1 at 512 + j, W2 at
+// 576 + j, b2 at 640).  All 32 lanes must call it.
+__device__ __forceinline__ float mlp_eval_tc(const float *x, const float *sw) {
+    const int lane = lane_id(), g = lane >> 2, tq = lane & 3;
+    // A fragments (row-major 16 x 8): a0 = (g, tq), a1 = (g + 8, tq),
+    // a2 = (g, tq + 4), a3 = (g + 8, tq + 4), rows taken from the lanes
+    // that hold them
+    uint32_t A[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        float ra[kMlpIn], rb[kMlpIn];
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) {
+            ra[k] = __shfl_sync(0xffffffffu, x[k], 16 * t + g);
+            rb[k] = __shfl_sync(0xffffffffu, x[k], 16 * t + g + 8);
+        }
+        A[t][0] = to_tf32(pick4(ra[0], ra[1], ra[2], ra[3], tq));
+        A[t][1] = to_tf32(pick4(rb[0], rb[1], rb[2], rb[3], tq));
+        A[t][2] = to_tf32(pick4(ra[4], ra[5], ra[6], ra[7], tq));
+        A[t][3] = to_tf32(pick4(rb[4], rb[5], rb[6], rb[7], tq));
+    }
+    float p[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};        // [tile][row g or g + 8]
+#pragma unroll
+    for (int nt = 0; nt < kMlpHid / 8; ++nt) {
+        // B fragment (column-major 8 x 8 of W1^T): b0 = (k = tq, n = g), b1 = (tq + 4, g)
+        const int j = nt * 8 + g;
+        const uint32_t b0 = __float_as_uint(sw[j * kMlpIn + tq]);
+        const uint32_t b1 = __float_as_uint(sw[j * kMlpIn + tq + 4]);
+        // accumulators: columns 2 tq, 2 tq + 1 of rows g (d0, d1) and g + 8 (d2, d3)
+        const int c0 = nt * 8 + 2 * tq, c1 = c0 + 1;
+        const float bb0 = sw[512 + c0], bb1 = sw[512 + c1];
+        const float ww0 = sw[576 + c0], ww1 = sw[576 + c1];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+            mma_tf32_m16n8k8(d0, d1, d2, d3, A[t][0], A[t][1], A[t][2], A[t][3], b0, b1);
+            p[t][0] = fmaf(ww0, fmaxf(d0 + bb0, 0.0f), p[t][0]);
+            p[t][0] = fmaf(ww1, fmaxf(d1 + bb1, 0.0f), p[t][0]);
+            p[t][1] = fmaf(ww0, fmaxf(d2 + bb0, 0.0f), p[t][1]);
+            p[t][1] = fmaf(ww1, fmaxf(d3 + bb1, 0.0f), p[t][1]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            p[t][h] += __shfl_xor_sync(0xffffffffu, p[t][h], 1);
+            p[t][h] += __shfl_xor_sync(0xffffffffu, p[t][h], 2);
+        }
+    // row r = 16 t + 8 h + g' is complete in lanes 4 g' .. 4 g' + 3
+    const int src = 4 * (lane & 7);
+    const float v00 = __shfl_sync(0xffffffffu, p[0][0], src);
+    const float v01 = __shfl_sync(0xffffffffu, p[0][1], src);
+    const float v10 = __shfl_sync(0xffffffffu, p[1][0], src);
+    const float v11 = __shfl_sync(0xffffffffu, p[1][1], src);
+    const int t = lane >> 4, h = (lane >> 3) & 1;
+    return sw[640] + (t == 0 ? (h == 0 ? v00 : v01) : (h == 0 ? v10 : v11));
 }
 
 __device__ __forceinline__ int32_t key_of(float s, int32_t key_bits) {
@@ -157,7 +248,7 @@ __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpP
                                                 int32_t cap, Load load, LearnQueue &Q,
                                                 unsigned long long &best_c, int32_t &best_m,
                                                 unsigned long long &bytes,
-                                                unsigned long long &evals) {
+                                                unsigned long long &evals, const float *sw) {
     const int w = warp_id(), lane = lane_id();
     int32_t *qm = Q.m[w], *qh = Q.h[w], *qi = Q.it[w];
     const int64_t in_n = a.noff[n + 1] - a.noff[n];
@@ -173,6 +264,28 @@ __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpP
         if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
         bytes += 20ull;
         evals += 1ull;
+    };
+    // tensor cores: the first `valid` queue slots at once (all lanes call it)
+    auto evaluate_tc = [&](int32_t valid) {
+        const bool ok = lane < valid;
+        float x[kMlpIn];
+        int32_t m = 0, h = 0;
+        if (ok) {
+            m = qm[lane];
+            h = qh[lane];
+            const int64_t in_m = a.noff[m + 1] - a.noff[m];
+            features(a, n, m, h, in_n + in_m - qi[lane], in_n, in_m, x);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kMlpIn; ++k) x[k] = 0.0f;
+        }
+        const float sc = mlp_eval_tc(x, sw);
+        if (ok) {
+            const unsigned long long c = composite(key_of(sc, M.key_bits), h);
+            if (best_m < 0 || c > best_c || (c == best_c && m > best_m)) { best_c = c; best_m = m; }
+            bytes += 20ull;
+            evals += 1ull;
+        }
     };
     int32_t qn = 0;                                      // warp-uniform queue length (< 32 here)
     for (int32_t base = w * 32; base < cap; base += kLearnThreads) {
@@ -194,7 +307,8 @@ __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpP
         qn += __popc(ball);
         __syncwarp();
         if (qn >= 32) {
-            evaluate(lane);
+            if (a.tc) evaluate_tc(32);
+            else evaluate(lane);
             __syncwarp();
             if (lane < qn - 32) {
                 qm[lane] = qm[32 + lane];
@@ -205,7 +319,11 @@ __device__ __forceinline__ void eval_candidates(const LearnedArgs &a, const MlpP
             qn -= 32;
         }
     }
-    if (lane < qn) evaluate(lane);
+    if (a.tc) {
+        if (qn > 0) evaluate_tc(qn);
+    } else if (lane < qn) {
+        evaluate(lane);
+    }
     __syncwarp();                                        // the queue is reused by the next node
 }
 
@@ -219,6 +337,9 @@ k_score_learned(LearnedArgs a, MlpParams M) {
     __shared__ int32_t s_i[kLearnWarps];
     __shared__ int32_t s_n, s_used;
     __shared__ LearnQueue s_queue;
+    __shared__ float s_w[kMlpParams];         // the network, for tensor-core evaluation
+    if (a.tc)
+        for (int i = threadIdx.x; i < kMlpParams; i += kLearnThreads) s_w[i] = a.tcw[i];
     // hash mode: the table is cleared once here, then only the slots a node
     // used (listed in gu) are visited and reset
     int32_t *gk = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
@@ -301,7 +422,7 @@ k_score_learned(LearnedArgs a, MlpParams M) {
                             if (DENSE) { m = i; h = hist[i]; it = inter[i]; }
                             else { int32_t sl = gu[i]; m = gk[sl]; h = gv[sl]; it = gi[sl]; }
                         },
-                        s_queue, best_c, best_m, bytes, evals);
+                        s_queue, best_c, best_m, bytes, evals, s_w);
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) {
             a.pair[n] = best_m;
@@ -340,6 +461,9 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
     __shared__ LearnQueue s_queue;
     __shared__ unsigned long long s_xc;
     __shared__ int32_t s_xi;
+    __shared__ float s_w[kMlpParams];         // the network, for tensor-core evaluation
+    if (a.tc)
+        for (int i = threadIdx.x; i < kMlpParams; i += kLearnThreads) s_w[i] = a.tcw[i];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int32_t id0 = rank * slice;
@@ -405,7 +529,7 @@ k_score_learned_cluster(LearnedArgs a, MlpParams M, int32_t slice) {
                             h = (int32_t)(v >> 16);
                             it = (int32_t)(v & 0xffffu);
                         },
-                        s_queue, best_c, best_m, bytes, evals);
+                        s_queue, best_c, best_m, bytes, evals, s_w);
         block_argmax(best_c, best_m, s_c, s_i);
         if (threadIdx.x == 0) { s_xc = best_c; s_xi = best_m; }
         for (int32_t i = threadIdx.x; i < len; i += kLearnThreads) cnt[i] = 0u;
@@ -484,7 +608,7 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
                               int64_t delta, const hgp_model *model, int32_t *pair,
                               int32_t *score, int32_t *key, int32_t *status,
                               unsigned long long *bytes, unsigned long long *evals,
-                              uint32_t debug, cudaStream_t s) {
+                              uint32_t debug, int32_t tensor_cores, cudaStream_t s) {
     if (L.V <= 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -501,6 +625,14 @@ cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int6
     cudaError_t e = dalloc(ar, &a.next, 1);
     if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
     if (e) return e;
+    if (tensor_cores) {           // W1, b1, W2, b2 are the first 641 floats of MlpParams
+        float *w = nullptr;
+        e = dalloc(ar, &w, kMlpParams);
+        if (!e) e = cudaMemcpyAsync(w, &M, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s);
+        if (e) return e;
+        a.tc = 1;
+        a.tcw = w;
+    }
     const int sms = num_sms();
     const size_t dense_smem = 2 * sizeof(int32_t) * (size_t)L.V;
     if (dense_smem + sizeof(LearnQueue) + 4096 <= (size_t)max_smem &&

@@ -86,8 +86,37 @@ static __global__ void k_bucket_lists(int32_t V, const int32_t *fit, const int32
     }
 }
 
-cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omega, int64_t delta,
-                      int32_t *pair, int32_t *score, int32_t *status,
+// Rows of the coarse level's in() bitmaps from the finer level's: coarse node
+// c is the finer node a = old_id[c] or the pair {a, match[a]}, and in(c) is
+// the union of its members' in(), so row(c) = row(a) | row(match[a]) (warp
+// per row, 16-byte words).
+static __global__ void k_bitmap_merge(int32_t V, int32_t words, const int32_t *old_id,
+                                      const int32_t *match_prev, const uint32_t *bm_prev,
+                                      uint32_t *bm) {
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t q = words >> 2;
+    for (int64_t c = gw; c < V; c += nw) {
+        const int32_t a = old_id[c], b = match_prev[a];
+        const uint4 *ra = reinterpret_cast<const uint4 *>(bm_prev + (int64_t)a * words);
+        const uint4 *rb = reinterpret_cast<const uint4 *>(bm_prev + (int64_t)b * words);
+        uint4 *rc = reinterpret_cast<uint4 *>(bm + c * words);
+        for (int32_t i = lane_id(); i < q; i += 32) {
+            uint4 x = ra[i];
+            if (b != a) {
+                const uint4 y = rb[i];
+                x.x |= y.x; x.y |= y.y; x.z |= y.z; x.w |= y.w;
+            }
+            rc[i] = x;
+        }
+    }
+}
+
+// roll: arena of this level's in() lists (the bitmaps are kept there, see
+// Level::bm); prev: the finer level (null at level 0), whose bitmaps, match
+// and this level's old_id let the rows be merged instead of rebuilt.
+cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const int32_t *ew,
+                      int64_t omega, int64_t delta, int32_t *pair, int32_t *score, int32_t *status,
                       unsigned long long *bytes, uint32_t debug, cudaStream_t s) {
     if (L.V <= 0) return cudaSuccess;
     int dev = 0;
@@ -111,16 +140,22 @@ cudaError_t run_score(Arena &ar, const Level &L, const int32_t *ew, int64_t omeg
     if (need_union && !(debug & HGP_DEBUG_NO_BITMAP) && words <= kBitmapMaxWords &&
         (int64_t)L.V * words * 4 <= bitmap_budget()) {
         uint32_t *bm = nullptr;
-        e = dalloc(ar, &bm, (size_t)L.V * words);
-        if (e) return e;
-        e = cudaMemsetAsync(bm, 0, sizeof(uint32_t) * (size_t)L.V * words, s);
+        e = dalloc(roll, &bm, (size_t)L.V * words);
         if (e) return e;
         int blocks = div_up((int64_t)L.V * 32, 256);
         if (blocks > num_sms() * 16) blocks = num_sms() * 16;
-        k_in_bitmap<<<blocks, 256, 0, s>>>(L.V, L.noff, L.inn, words, bm);
+        if (prev && prev->bm && prev->bm_words == words && L.old_id && prev->match) {
+            k_bitmap_merge<<<blocks, 256, 0, s>>>(L.V, words, L.old_id, prev->match, prev->bm, bm);
+        } else {
+            e = cudaMemsetAsync(bm, 0, sizeof(uint32_t) * (size_t)L.V * words, s);
+            if (e) return e;
+            k_in_bitmap<<<blocks, 256, 0, s>>>(L.V, L.noff, L.inn, words, bm);
+        }
         count_launch();
         a.bm = bm;
         a.bm_words = words;
+        L.bm = bm;
+        L.bm_words = words;
     }
     size_t row_bytes = sizeof(uint32_t) * (size_t)a.bm_words;
     size_t dense_smem = row_bytes + sizeof(int32_t) * (size_t)L.V;

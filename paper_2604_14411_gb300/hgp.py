@@ -54,7 +54,8 @@ class hgp_model(ctypes.Structure):
 class hgp_options(ctypes.Structure):
     _fields_ = [("refine_passes", ctypes.c_int32), ("debug", ctypes.c_uint32),
                 ("max_levels", ctypes.c_int32), ("matching", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2), ("model", ctypes.POINTER(hgp_model))]
+                ("learned_eval", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+                ("model", ctypes.POINTER(hgp_model))]
 
 
 class hgp_train_options(ctypes.Structure):
@@ -85,8 +86,8 @@ def _c_model(model):
     return m
 
 
-def _options(refine_passes, debug, max_levels, model, matching=0):
-    opt = hgp_options(refine_passes, debug, max_levels, matching)
+def _options(refine_passes, debug, max_levels, model, matching=0, learned_eval=0):
+    opt = hgp_options(refine_passes, debug, max_levels, matching, learned_eval)
     cm = _c_model(model)
     if cm is not None:
         opt.model = ctypes.pointer(cm)
@@ -295,12 +296,13 @@ def hgp_create(num_nodes, offsets, pins, node_weights=None, edge_weights=None, s
 
 
 def hgp_partition(handle, omega, delta, part_ids, part_weight=None, part_inbound=None,
-                  refine_passes=1, debug=0, max_levels=0, model=None, matching=0):
+                  refine_passes=1, debug=0, max_levels=0, model=None, matching=0, learned_eval=0):
     """hgp_partition into caller buffers (host numpy or device torch tensors).
     matching=1: the exact maximum-weight matching instead of the two walks.
+    learned_eval=1 (with a model): the network's hidden layer on tensor cores.
     Returns (cost, num_parts, num_levels)."""
     lib = load()
-    opt, _keep = _options(refine_passes, debug, max_levels, model, matching)
+    opt, _keep = _options(refine_passes, debug, max_levels, model, matching, learned_eval)
     res = hgp_result()
     res.part_ids = _ptr(part_ids)
     res.part_weight = _ptr(part_weight)
@@ -423,12 +425,12 @@ class Graph:
                    allocator, outbound)
 
     def partition(self, omega, delta, refine_passes=1, debug=0, max_levels=0, model=None,
-                  matching=0) -> Result:
+                  matching=0, learned_eval=0) -> Result:
         ids = np.empty(self.num_nodes, dtype=np.int32)
         pw = np.empty(self.num_nodes, dtype=np.int64)
         pin = np.empty(self.num_nodes, dtype=np.int32)
         cost, npart, nlev = hgp_partition(self._h, omega, delta, ids, pw, pin, refine_passes, debug,
-                                          max_levels, model, matching)
+                                          max_levels, model, matching, learned_eval)
         return Result(ids, cost, npart, nlev, pw[:npart], pin[:npart])
 
     def partition_device(self, omega, delta, part_ids, part_weight=None, part_inbound=None,

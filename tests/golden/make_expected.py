@@ -4,6 +4,8 @@ generators; nothing here touches the CUDA library.
 
     python tests/golden/make_expected.py snn16k     # 16,384-node SNN, Omega 2^10, Delta 2^12
     python tests/golden/make_expected.py batch64    # 39 members of the 64-instance batch
+    python tests/golden/make_expected.py batch64 4,52,30 --jobs 6
+        # more members, one oracle run per worker process, merged into the file
 
 Output: tests/golden/expected_<name>.txt with the Eq. (1) cost, the number of
 parts, the number of levels, the per-level node counts, and a SHA-256 of
@@ -60,8 +62,42 @@ def batch64():
     print(path)
 
 
+def _member_line(i):
+    """One member's result line (runs in a worker process)."""
+    g = synth.batch_instances(64, 0)[i]
+    t = time.time()
+    with oracle.Run.from_graph(g) as r:
+        res = r.partition(1024, 4096)
+        nlev = r.num_levels
+    stats = np.stack([res.part_weight.astype(np.int64), res.part_inbound.astype(np.int64)], axis=1)
+    return i, (f"{i}: {res.cost} {res.num_parts} {nlev} {digest(res.part_ids.astype('<i4'))} "
+               f"{digest(stats.astype('<i8'))}  # {g.name}, {time.time() - t:.0f} s")
+
+
+def batch64_more(members, jobs):
+    """Adds the listed members to expected_batch64.txt, keeping the lines
+    already there; each finished member is written at once."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    path = os.path.join(ROOT, "tests", "golden", "expected_batch64.txt")
+    with cf.ProcessPoolExecutor(max_workers=jobs, mp_context=mp.get_context("spawn")) as ex:
+        for fut in cf.as_completed([ex.submit(_member_line, i) for i in members]):
+            i, line = fut.result()
+            with open(path) as f:
+                lines = [l.rstrip("\n") for l in f]
+            head = [l for l in lines if l.startswith("#")]
+            body = {int(l.split(":", 1)[0]): l for l in lines if l and not l.startswith("#")}
+            body[i] = line
+            with open(path, "w") as f:
+                f.write("\n".join(head + [body[k] for k in sorted(body)]) + "\n")
+            print(line, flush=True)
+
+
 def main(name: str):
     if name == "batch64":
+        if len(sys.argv) > 2:
+            jobs = int(sys.argv[sys.argv.index("--jobs") + 1]) if "--jobs" in sys.argv else 1
+            return batch64_more([int(x) for x in sys.argv[2].split(",")], jobs)
         return batch64()
     make, omega, delta = WORKLOADS[name]
     g = make()

@@ -212,3 +212,67 @@ def test_trained_model_partitions_are_feasible():
     assert sorted(st) == list(range(res.num_parts))
     assert [st[p][1] for p in range(res.num_parts)] == res.part_inbound.tolist()
     assert plain.cost > 0 and res.cost > 0
+
+
+def _tol(s):
+    """Score tolerance of the tensor-core mode: 1e-2 relative, at least 1e-2
+    absolute (a key step at key_bits = 6 is 1/64)."""
+    return 1e-2 * max(1.0, abs(s))
+
+
+@pytest.mark.parametrize("seed,scale", [(31, 0.5), (32, 1.0), (33, 0.25)])
+def test_tensor_core_scores_within_tolerance(seed, scale):
+    """learned_eval = 1: the network's hidden layer on tensor cores (TF32
+    inputs, float32 accumulation).  With key_bits = 20 a key carries its
+    score to 2^-20.  On every first-level node: a node with no valid
+    neighbour has none either way (the checks are exact); otherwise the
+    chosen neighbour is valid, its tensor-core score matches the float32
+    oracle's score of the same pair within the tolerance, and that float32
+    score is within the tolerance of the best the float32 order finds."""
+    from brute import in_sets
+    g = synth.random_snn(1200, 20, seed)
+    omega, delta = 40, 240
+    model = synth.random_model(seed, scale, 20)
+    with hgp.Graph.from_hypergraph(g) as G:
+        G.partition(omega, delta, 0, debug=H.HGP_DEBUG_KEEP_LEVELS, max_levels=1, model=model,
+                    learned_eval=1)
+        pair = G.level_array(0, H.HGP_LEVEL_PAIR)
+        key = G.level_array(0, H.HGP_LEVEL_KEY)
+    ins = in_sets(g.num_nodes, g.offsets, g.pins)
+    checked = 0
+    with oracle.Run.from_graph(g) as r:
+        rp, _, rk = r.score0_learned_nodes(omega, delta, model, np.arange(g.num_nodes))
+        for n in range(g.num_nodes):
+            m = int(pair[n])
+            if rp[n] < 0:
+                assert m == -1
+                continue
+            assert m >= 0 and m != n
+            assert 2 <= omega and len(ins[n] | ins[m]) <= delta
+            s_ref, _ = oracle.mlp(model, r.features0(n, m))
+            s_tc = key[n] / 2.0 ** 20
+            assert abs(s_tc - s_ref) <= _tol(s_ref) + 2.0 ** -19, (n, m, s_tc, s_ref)
+            s_best = rk[n] / 2.0 ** 20
+            assert s_ref >= s_best - 2 * _tol(s_best) - 2.0 ** -19, (n, s_ref, s_best)
+            checked += 1
+    assert checked > g.num_nodes // 2
+
+
+def test_tensor_core_partitions_are_feasible():
+    """Whole partitions with the tensor-core evaluation, dense and cluster
+    scorers: feasible, cost recounted, and close to the FMA-chain order's."""
+    g = synth.random_snn(3000, 24, 7)
+    omega, delta = 48, 300
+    model = synth.random_model(5, 0.5, 6)
+    for debug in (0, H.HGP_DEBUG_FORCE_CLUSTER):
+        with hgp.Graph.from_hypergraph(g) as G:
+            tc = G.partition(omega, delta, debug=debug, model=model, learned_eval=1)
+            fma = G.partition(omega, delta, debug=debug, model=model)
+        assert conn(g.offsets, g.pins, tc.part_ids) == tc.cost
+        st = part_stats(g.num_nodes, g.offsets, g.pins, tc.part_ids)
+        assert all(w <= omega and d <= delta for w, d in st.values())
+        assert abs(tc.cost - fma.cost) <= 0.05 * fma.cost
+    with hgp.Graph.from_hypergraph(g) as G:
+        with pytest.raises(H.HgpError) as ei:
+            G.partition(omega, delta, learned_eval=1)          # no model
+        assert ei.value.code == H.HGP_ERR_INVALID_ARG
