@@ -14,7 +14,8 @@
 namespace hgp {
 cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const int32_t *ew,
                       int64_t omega, int64_t delta, int32_t *pair, int32_t *score, int32_t *status,
-                      unsigned long long *bytes, uint32_t debug, cudaStream_t s);
+                      unsigned long long *bytes, uint32_t debug, int64_t bm_budget, cudaStream_t s);
+int64_t bitmap_budget();
 cudaError_t run_score_learned(Arena &ar, const Level &L, const int32_t *ew, int64_t omega,
                               int64_t delta, const hgp_model *model, int32_t *pair,
                               int32_t *score, int32_t *key, int32_t *status,
@@ -337,6 +338,7 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         a->min_chunk = (size_t)64 << 20;
     }
     size_t inc_budget = 0, inc_kept = 0;
+    const int64_t bm_budget = model ? 0 : bitmap_budget();     // in() bitmaps per level
     if (!(debug & HGP_DEBUG_REBUILD_INC)) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) inc_budget = fr / 10 * 4;   // 40 % of free
@@ -406,8 +408,8 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
                                       debug, learned_eval, s), "score");
             else
                 CKP(run_score(tmp, roll[l & 1], L, l > 0 ? &levels[l - 1] : nullptr, g->ew, omega,
-                              delta, pair, score, d_status, tm.on ? d_bytes : nullptr, debug, s),
-                    "score");
+                              delta, pair, score, d_status, tm.on ? d_bytes : nullptr, debug,
+                              bm_budget, s), "score");
             tm.stop(0, ev_a);
             tm.start(1, &ev_a);
             CKP(run_match(tmp, L.V, pair, score, key, L.match, L.gamma, d_V2, d_status, s,

@@ -135,6 +135,82 @@ __global__ void k_runs(int32_t E, const int32_t *poff, PartsView pv,
     }
 }
 
+// The same runs for levels whose hyperedges have at most kRunsEdgeMax pins,
+// without the global sort: a warp loads the parts of its hyperedge's pins
+// into shared memory, sorts them (bitonic, padded to a power of two), and
+// cuts the sorted parts into runs -- the ascending (part, count) sequence the
+// stable sort by (edge, part) gives.
+constexpr int kRunsEdgeMax = 256;
+constexpr int kRunsWarps = 8;
+
+__global__ void __launch_bounds__(kRunsWarps * 32)
+k_runs_small(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *src,
+             const uint8_t *sdst, const int32_t *rho, int32_t *rpart, int32_t *rcnt,
+             int32_t *rcin, int32_t *rpos, int32_t *nrun, int32_t *inb, int32_t K,
+             int32_t use_smem) {
+    extern __shared__ int32_t inb_s[];       // per-CTA inbound counts (use_smem)
+    __shared__ int32_t buf[kRunsWarps][kRunsEdgeMax];
+    if (use_smem) {
+        for (int32_t i = threadIdx.x; i < K; i += blockDim.x) inb_s[i] = 0;
+        __syncthreads();
+    }
+    const int w = warp_id(), lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t *b = buf[w];
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = gw; e < E; e += nw) {
+        const int32_t p0 = poff[e], p1 = poff[e + 1], len = p1 - p0;
+        int32_t sz = 32;
+        while (sz < len) sz <<= 1;
+        for (int32_t i = lane; i < sz; i += 32) b[i] = i < len ? rho[pins[p0 + i]] : 0x7fffffff;
+        __syncwarp();
+        for (int32_t k = 2; k <= sz; k <<= 1)
+            for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                for (int32_t i = lane; i < sz; i += 32) {
+                    const int32_t x = i ^ j;
+                    if (x > i) {
+                        const int32_t u = b[i], v = b[x];
+                        if ((u > v) == ((i & k) == 0)) { b[i] = v; b[x] = u; }
+                    }
+                }
+                __syncwarp();
+            }
+        int32_t r = 0;
+        for (int32_t base = 0; base < len; base += 32) {
+            const int32_t i = base + lane;
+            const bool st = i < len && (i == 0 || b[i - 1] != b[i]);
+            const unsigned ball = __ballot_sync(0xffffffffu, st);
+            if (st) {
+                const int32_t q = p0 + r + __popc(ball & lt);
+                rpart[q] = b[i];
+                rpos[q] = i;
+            }
+            r += __popc(ball);
+        }
+        __syncwarp();
+        const int32_t srcpart = rho[src[e]];
+        const uint8_t role = sdst[e];
+        for (int32_t q = lane; q < r; q += 32) {
+            const int32_t end = (q + 1 < r) ? rpos[p0 + q + 1] : len;
+            const int32_t c = end - rpos[p0 + q];
+            const int32_t p = rpart[p0 + q];
+            const int32_t has_src = p == srcpart ? 1 : 0;
+            const int32_t ci = ((role & 2) ? c - has_src : 0) + ((role & 1) ? has_src : 0);
+            rcnt[p0 + q] = c;
+            rcin[p0 + q] = ci;
+            if (inb && ci > 0) atomicAdd(use_smem ? &inb_s[p] : &inb[p], 1);
+        }
+        if (lane == 0) nrun[e] = r;
+        __syncwarp();                        // b is reused by the warp's next hyperedge
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < K; i += blockDim.x)
+            if (inb_s[i]) atomicAdd(&inb[i], inb_s[i]);
+    }
+}
+
 struct Runs {
     int32_t *rpart, *rcnt, *rcin, *nrun;
 };
@@ -150,6 +226,24 @@ static cudaError_t build_runs(Arena &tmp, const Level &L, const int32_t *rho, in
     if (!e) e = dalloc(tmp, &R.rcin, P);
     if (!e) e = dalloc(tmp, &R.nrun, L.E);
     if (e) return e;
+    if (L.max_edge <= kRunsEdgeMax) {
+        if (L.E > 0) {
+            const int32_t use_smem = (inb && K <= 16384) ? 1 : 0;
+            const size_t smem = use_smem ? sizeof(int32_t) * (size_t)K : 0;
+            int blocks = div_up((int64_t)L.E * 32, kRunsWarps * 32);
+            if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+            if (use_smem && blocks > num_sms() * 4) blocks = num_sms() * 4;   // fewer flushes
+            if (use_smem) {
+                cudaError_t ea = allow_dynamic_smem(k_runs_small);
+                if (ea) return ea;
+            }
+            k_runs_small<<<blocks, kRunsWarps * 32, smem, s>>>(L.E, L.poff, L.pins, L.src, L.sdst,
+                                                               rho, R.rpart, R.rcnt, R.rcin, rpos,
+                                                               R.nrun, inb, K, use_smem);
+            count_launch();
+        }
+        return cudaGetLastError();
+    }
     expand_rows(L.poff, L.E, row_of, s);
     PartsView pv{nullptr, nullptr, K};
     if ((int64_t)L.E * K <= (int64_t)UINT32_MAX) {
@@ -438,6 +532,81 @@ __global__ void k_move_deg1(int32_t Mcap, const int32_t *dM, const int32_t *mv_n
          k += (int64_t)gridDim.x * blockDim.x) {
         int32_t n = k < M ? mv_n[k] : -1;
         deg[k] = n >= 0 ? ioff[n + 1] - ioff[n] : 0;
+    }
+}
+
+// Same computation with each mover packed into one 64-bit word (move index,
+// ps, pd: 21 bits each; the destination bit) when every id fits 21 bits:
+// the quadratic scan then reads one broadcast shared-memory word per earlier
+// mover and updates the counts without branching.
+constexpr int kSeqPackBits = 21;
+constexpr unsigned long long kSeqPackMask = (1ull << kSeqPackBits) - 1ull;
+
+__global__ void __launch_bounds__(kSeqWarps * 32)
+k_seq_edge_packed(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *idx_of,
+                  const int32_t *mv_ps, const int32_t *mv_pd, const int32_t *src,
+                  const uint8_t *sdst, const int32_t *ioff, const int32_t *inc,
+                  const int32_t *slot0, const int32_t *nrun, const int32_t *rpart,
+                  const int32_t *rcnt, const int32_t *rcin, const int32_t *ew, int32_t *c_gain,
+                  uint8_t *c_in) {
+    __shared__ unsigned long long spk[kSeqWarps][kSeqEdgeMax];
+    __shared__ int32_t sn[kSeqWarps][kSeqEdgeMax];
+    const int w = warp_id();
+    const unsigned lt = (1u << lane_id()) - 1u;
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = gw; e < E; e += nw) {
+        const int32_t p0 = poff[e], p1 = poff[e + 1];
+        const int32_t se = src[e];
+        const uint8_t role = sdst[e];
+        int32_t cnt = 0;
+        for (int32_t base = p0; base < p1; base += 32) {
+            const int32_t j = base + lane_id();
+            const int32_t m = j < p1 ? pins[j] : -1;
+            const int32_t k = m >= 0 ? idx_of[m] : -1;
+            const unsigned ball = __ballot_sync(0xffffffffu, k >= 0);
+            if (k >= 0) {
+                const int32_t q = cnt + __popc(ball & lt);
+                spk[w][q] = ((unsigned long long)k << (2 * kSeqPackBits + 1)) |
+                            ((unsigned long long)mv_ps[k] << (kSeqPackBits + 1)) |
+                            ((unsigned long long)mv_pd[k] << 1) |
+                            (counts_in(m, se, role) ? 1ull : 0ull);
+                sn[w][q] = m;
+            }
+            cnt += __popc(ball);
+        }
+        __syncwarp();
+        const int32_t r0 = poff[e], r1 = r0 + nrun[e];
+        const int32_t we = ew[e];
+        for (int32_t i = lane_id(); i < cnt; i += 32) {
+            const unsigned long long ui = spk[w][i];
+            const int32_t ki = (int32_t)(ui >> (2 * kSeqPackBits + 1));
+            const int32_t psi = (int32_t)((ui >> (kSeqPackBits + 1)) & kSeqPackMask);
+            const int32_t pdi = (int32_t)((ui >> 1) & kSeqPackMask);
+            int32_t cs, csi, cd, cdi;
+            run_lookup(rpart, rcnt, rcin, r0, r1, psi, cs, csi);
+            run_lookup(rpart, rcnt, rcin, r0, r1, pdi, cd, cdi);
+            for (int32_t t = 0; t < cnt; ++t) {
+                const unsigned long long u = spk[w][t];
+                const int32_t before = (int32_t)(u >> (2 * kSeqPackBits + 1)) < ki ? 1 : 0;
+                const int32_t ps = (int32_t)((u >> (kSeqPackBits + 1)) & kSeqPackMask);
+                const int32_t pd = (int32_t)((u >> 1) & kSeqPackMask);
+                const int32_t ds = before * ((pd == psi) - (ps == psi));
+                const int32_t dd = before * ((pd == pdi) - (ps == pdi));
+                const int32_t dt = (int32_t)(u & 1ull);
+                cs += ds;
+                cd += dd;
+                csi += dt * ds;
+                cdi += dt * dd;
+            }
+            const int32_t n = sn[w][i];
+            const int32_t pos = lower_bound_i32(inc, ioff[n], ioff[n + 1], (int32_t)e) - ioff[n];
+            const int32_t sl = slot0[ki] + pos;
+            const bool dst = (ui & 1ull) != 0;
+            c_gain[sl] = we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
+            c_in[sl] = (uint8_t)(((dst && csi == 1) ? 1 : 0) | ((dst && cdi == 0) ? 2 : 0));
+        }
+        __syncwarp();
     }
 }
 
@@ -889,9 +1058,15 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
         int blocks = div_up((int64_t)L.E * 32, kSeqWarps * 32);
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         if (blocks < 1) blocks = 1;
-        k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_n, mv_ps, mv_pd,
-                                                     L.src, L.sdst, L.ioff, L.inc, slot0, R.nrun,
-                                                     R.rpart, R.rcnt, R.rcin, ew, c_gain, c_in);
+        if ((int64_t)V < (1ll << kSeqPackBits) && (int64_t)K < (1ll << kSeqPackBits))
+            k_seq_edge_packed<<<blocks, kSeqWarps * 32, 0, s>>>(
+                L.E, L.poff, L.pins, idx_of, mv_ps, mv_pd, L.src, L.sdst, L.ioff, L.inc, slot0,
+                R.nrun, R.rpart, R.rcnt, R.rcin, ew, c_gain, c_in);
+        else
+            k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_n, mv_ps,
+                                                         mv_pd, L.src, L.sdst, L.ioff, L.inc, slot0,
+                                                         R.nrun, R.rpart, R.rcnt, R.rcin, ew, c_gain,
+                                                         c_in);
         count_launch();
         k_move_reduce1<<<grid_warps(M), 256, 0, s>>>(M, slot0, c_gain, c_in, gseq, lose, gin);
         count_launch();

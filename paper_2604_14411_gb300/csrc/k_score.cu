@@ -7,10 +7,11 @@ namespace hgp {
 
 bool launch_score_cluster(const ScoreArgs &a, int max_smem, cudaStream_t s, cudaError_t *err);
 
-// bytes of in() bitmaps per level: a tenth of the free device memory, at
-// most 16 GiB (a popcount over two rows is far cheaper than searching sorted
-// in() lists once unions grow to thousands of hyperedges)
-static int64_t bitmap_budget() {
+// bytes of in() bitmaps per level: a tenth of the device memory free when
+// the partition started, at most 16 GiB (a popcount over two rows is far
+// cheaper than searching sorted in() lists once unions grow to thousands of
+// hyperedges); measured once per partition by the caller
+int64_t bitmap_budget() {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 1ll << 30;
     int64_t b = (int64_t)(fr / 10);
@@ -117,7 +118,7 @@ static __global__ void k_bitmap_merge(int32_t V, int32_t words, const int32_t *o
 // and this level's old_id let the rows be merged instead of rebuilt.
 cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const int32_t *ew,
                       int64_t omega, int64_t delta, int32_t *pair, int32_t *score, int32_t *status,
-                      unsigned long long *bytes, uint32_t debug, cudaStream_t s) {
+                      unsigned long long *bytes, uint32_t debug, int64_t bm_budget, cudaStream_t s) {
     if (L.V <= 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -138,7 +139,7 @@ cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const
     int32_t words = ((L.E + 31) / 32 + 3) & ~3;
     bool need_union = 2 * (int64_t)L.max_in > delta;
     if (need_union && !(debug & HGP_DEBUG_NO_BITMAP) && words <= kBitmapMaxWords &&
-        (int64_t)L.V * words * 4 <= bitmap_budget()) {
+        (int64_t)L.V * words * 4 <= bm_budget) {
         uint32_t *bm = nullptr;
         e = dalloc(roll, &bm, (size_t)L.V * words);
         if (e) return e;
@@ -224,16 +225,19 @@ cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const
         if (e) return e;
     }
     if (dense) {
-        e = allow_dynamic_smem(k_score<true>);
+        // (two 512-thread CTAs per SM were measured: slower on the 16k SNN,
+        // 164 -> 197 ms of scoring per step)
+        auto kern = k_score<true, kScoreThreads>;
+        const int nt = kScoreThreads;
+        e = allow_dynamic_smem(kern);
         if (e) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<true>, kScoreThreads,
-                                                          dense_smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, dense_smem);
         if (e) return e;
         if (per_sm < 1) per_sm = 1;
         int blocks = sms * per_sm;
         if (blocks > L.V) blocks = L.V;
-        k_score<true><<<blocks, kScoreThreads, dense_smem, s>>>(a);
+        kern<<<blocks, nt, dense_smem, s>>>(a);
         count_launch();
         return cudaGetLastError();
     }

@@ -72,6 +72,7 @@ __device__ __forceinline__ uint32_t hash_u32(uint32_t x) {
     return x;
 }
 
+template <int NW = kScoreWarps>
 __device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -80,7 +81,7 @@ __device__ __forceinline__ int32_t block_max_i32(int32_t v, int32_t *red) {
     __syncthreads();
     int32_t r = red[0];
 #pragma unroll
-    for (int i = 1; i < kScoreWarps; ++i) r = max(r, red[i]);
+    for (int i = 1; i < NW; ++i) r = max(r, red[i]);
     return r;
 }
 
@@ -170,7 +171,8 @@ __device__ __forceinline__ void warp_accumulate(const ScoreArgs &a, int32_t n, i
     }
 }
 
-// CTA-wide maxima of two values at once (red: 2 * kScoreWarps entries).
+// CTA-wide maxima of two values at once over NW warps (red: 2 * NW entries).
+template <int NW = kScoreWarps>
 __device__ __forceinline__ void block_max2_i32(int32_t &x, int32_t &y, int32_t *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -178,12 +180,12 @@ __device__ __forceinline__ void block_max2_i32(int32_t &x, int32_t &y, int32_t *
         y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
     }
     __syncthreads();
-    if (lane_id() == 0) { red[warp_id()] = x; red[kScoreWarps + warp_id()] = y; }
+    if (lane_id() == 0) { red[warp_id()] = x; red[NW + warp_id()] = y; }
     __syncthreads();
     x = red[0];
-    y = red[kScoreWarps];
+    y = red[NW];
 #pragma unroll
-    for (int i = 1; i < kScoreWarps; ++i) { x = max(x, red[i]); y = max(y, red[kScoreWarps + i]); }
+    for (int i = 1; i < NW; ++i) { x = max(x, red[i]); y = max(y, red[NW + i]); }
 }
 
 // Warp-cooperative validity test of pair (n, m); all lanes return the same.
@@ -225,14 +227,18 @@ static __device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, cons
     return extra <= room;
 }
 
-template <bool DENSE>
-__global__ void __launch_bounds__(kScoreThreads)
+// NT threads per CTA: 1024 (one CTA per SM), or 512 with two CTAs per SM when
+// two histograms fit (shorter barriers, one CTA's extraction overlapping the
+// other's gather).
+template <bool DENSE, int NT = kScoreThreads>
+__global__ void __launch_bounds__(NT, kScoreThreads / NT)
 k_score(ScoreArgs a) {
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: [row of in(n): bm_words][dense hist V]
     uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
     int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
-    __shared__ int32_t red[2 * kScoreWarps];
+    __shared__ int32_t red[2 * NW];
 
     int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
     int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
@@ -257,25 +263,25 @@ k_score(ScoreArgs a) {
         const int32_t base = (DENSE && a.wlo) ? a.wlo[n] : 0;
         const int32_t cap = DENSE ? (a.wlo ? max(0, a.whi[n] - base + 1) : a.V) : a.gcap;
         // ---- clear; stage row(n) ----
-        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+        for (int32_t i = threadIdx.x; i < cap; i += NT) {
             if (DENSE) hist[i] = 0;
             else { gkeys[i] = -1; gvals[i] = 0; }
         }
         if (a.bm_words) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.bm + (int64_t)n * a.bm_words);
             uint4 *dst = reinterpret_cast<uint4 *>(row_n);
-            for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += kScoreThreads) dst[i] = src[i];
+            for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += NT) dst[i] = src[i];
         }
         __syncthreads();
         // ---- Eq. (2) accumulation: warp w takes hyperedges i0 + w, i0 + w + W, ... ----
         {
             const int32_t i0 = a.ioff[n], deg = a.ioff[n + 1] - i0;
-            const int32_t mine = (deg - warp_id() + kScoreWarps - 1) / kScoreWarps;
+            const int32_t mine = (deg - warp_id() + NW - 1) / NW;
             if (DENSE) {
-                warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
+                warp_accumulate(a, n, i0, warp_id(), NW, mine,
                                 [&](int32_t m, int32_t wt) { atomicAdd(&hist[m - base], wt); }, bytes);
             } else {
-                warp_accumulate(a, n, i0, warp_id(), kScoreWarps, mine,
+                warp_accumulate(a, n, i0, warp_id(), NW, mine,
                                 [&](int32_t m, int32_t wt) {
                                     uint32_t slot = hash_u32((uint32_t)m) & mask;
                                     for (int32_t probes = 0;;) {
@@ -295,7 +301,7 @@ k_score(ScoreArgs a) {
         // table in shared memory alone, checking the tie group of value hmax
         // and finding the next lower value in the same pass.
         int32_t hmax = 0;
-        for (int32_t i = threadIdx.x; i < cap; i += kScoreThreads) {
+        for (int32_t i = threadIdx.x; i < cap; i += NT) {
             const int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
             if (h <= 0) continue;
             if (!eligible(a, DENSE ? base + i : gkeys[i], h, thr)) {
@@ -304,10 +310,10 @@ k_score(ScoreArgs a) {
                 hmax = max(hmax, h);
             }
         }
-        hmax = block_max_i32(hmax, red);
+        hmax = block_max_i32<NW>(hmax, red);
         const int64_t in_n = a.noff[n + 1] - a.noff[n];
         int32_t result = -1, rscore = 0;
-        const int32_t per_warp = (((cap + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
+        const int32_t per_warp = (((cap + NW - 1) / NW) + 31) & ~31;
         const int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
         while (hmax > 0) {
             // every neighbour with hist == hmax, one warp per candidate; nxt =
@@ -345,7 +351,7 @@ k_score(ScoreArgs a) {
                     }
                 }
             }
-            block_max2_i32(best_id, nxt, red);
+            block_max2_i32<NW>(best_id, nxt, red);
             if (best_id >= 0) { result = best_id; rscore = hmax; break; }
             hmax = nxt;
         }
