@@ -188,6 +188,30 @@ __device__ __forceinline__ void block_max2_i32(int32_t &x, int32_t &y, int32_t *
     for (int i = 1; i < NW; ++i) { x = max(x, red[i]); y = max(y, red[NW + i]); }
 }
 
+// CTA-wide maxima of a 64-bit key and a 32-bit value over NW warps.
+template <int NW = kScoreWarps>
+__device__ __forceinline__ void block_max_key(unsigned long long &k, int32_t &x,
+                                              unsigned long long *red64, int32_t *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        k = k2 > k ? k2 : k;
+        x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    }
+    __syncthreads();
+    if (lane_id() == 0) { red64[warp_id()] = k; red[warp_id()] = x; }
+    __syncthreads();
+    k = red64[0];
+    x = red[0];
+#pragma unroll
+    for (int i = 1; i < NW; ++i) { k = red64[i] > k ? red64[i] : k; x = max(x, red[i]); }
+}
+
+// Candidate key in the extraction order: (hist, id), larger first.
+__device__ __forceinline__ unsigned long long cand_key(int32_t h, int32_t id) {
+    return ((unsigned long long)(uint32_t)h << 32) | (uint32_t)id;
+}
+
 // Warp-cooperative validity test of pair (n, m); all lanes return the same.
 static __device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, const uint32_t *row_n,
                            int64_t in_n, unsigned long long &bytes) {
@@ -239,6 +263,7 @@ k_score(ScoreArgs a) {
     uint32_t *row_n = reinterpret_cast<uint32_t *>(smem);
     int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
     __shared__ int32_t red[2 * NW];
+    __shared__ unsigned long long red64[NW];
 
     int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
     int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
@@ -315,45 +340,61 @@ k_score(ScoreArgs a) {
         int32_t result = -1, rscore = 0;
         const int32_t per_warp = (((cap + NW - 1) / NW) + 31) & ~31;
         const int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
-        while (hmax > 0) {
-            // every neighbour with hist == hmax, one warp per candidate; nxt =
-            // the largest value below hmax (complete whenever no warp found a
-            // valid candidate, since only a find ends a warp's scan early)
-            int32_t best_id = -1, nxt = 0;
+        // Rounds over bands of values [bot, top]: every candidate in the band
+        // is checked and the largest valid (hist, id) wins -- the first valid
+        // one in the (hist desc, id desc) order, since every value above the
+        // band has been checked already.  The first band is the top value
+        // alone; after each round without a valid candidate the band doubles
+        // (a node facing saturated clusters fails many groups in a row).  nxt
+        // = the largest value below the band, complete whenever no warp ended
+        // its scan early (only a find at the band's top ends it).
+        int32_t top = hmax, width = 1;
+        while (top > 0) {
+            const int32_t bot = max(1, top - width + 1);
+            unsigned long long best = 0ull;           // this warp's best valid key
+            int32_t nxt = 0;
             if (DENSE) {
-                // ids are table indices: scan downwards, the first valid is this warp's best
-                for (int32_t b0 = lo + ((hi - lo - 1) & ~31); b0 >= lo && best_id < 0; b0 -= 32) {
+                // ids are table indices: scan downwards, so within one value the
+                // first valid candidate is the warp's best
+                for (int32_t b0 = lo + ((hi - lo - 1) & ~31); b0 >= lo; b0 -= 32) {
                     const int32_t i = b0 + lane_id();
                     const int32_t h = i < hi ? hist[i] : 0;
-                    if (h < hmax) nxt = max(nxt, h);
-                    unsigned ball = __ballot_sync(0xffffffffu, h == hmax);
-                    while (ball && best_id < 0) {
-                        int src = 31 - __clz(ball);
+                    if (h < bot) nxt = max(nxt, h);
+                    const unsigned long long key = cand_key(h, base + i);
+                    unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
+                    while (ball) {
+                        const int src = 31 - __clz(ball);
                         ball &= ~(1u << src);
-                        if (warp_check(a, n, base + b0 + src, row_n, in_n, bytes)) best_id = base + b0 + src;
+                        const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
+                        if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
+                            best = ck;
                     }
+                    if ((int32_t)(best >> 32) == top) break;   // nothing in the band beats it
                 }
             } else {
                 for (int32_t b0 = lo; b0 < hi; b0 += 32) {
                     const int32_t i = b0 + lane_id();
-                    int32_t m = -1, h = 0;
+                    int32_t h = 0;
+                    unsigned long long key = 0ull;
                     if (i < hi && gkeys[i] >= 0) {
                         h = gvals[i];
-                        if (h == hmax) m = gkeys[i];
-                        else if (h < hmax) nxt = max(nxt, h);
+                        key = cand_key(h, gkeys[i]);
+                        if (h < bot) nxt = max(nxt, h);
                     }
-                    unsigned ball = __ballot_sync(0xffffffffu, m >= 0);
+                    unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
                     while (ball) {
-                        int src = __ffs(ball) - 1;
+                        const int src = __ffs(ball) - 1;
                         ball &= ball - 1;
-                        int32_t cm = __shfl_sync(0xffffffffu, m, src);
-                        if (cm > best_id && warp_check(a, n, cm, row_n, in_n, bytes)) best_id = cm;
+                        const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
+                        if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
+                            best = ck;
                     }
                 }
             }
-            block_max2_i32<NW>(best_id, nxt, red);
-            if (best_id >= 0) { result = best_id; rscore = hmax; break; }
-            hmax = nxt;
+            block_max_key<NW>(best, nxt, red64, red);
+            if (best) { result = (int32_t)(best & 0xffffffffu); rscore = (int32_t)(best >> 32); break; }
+            top = nxt;
+            width <<= 1;
         }
         if (threadIdx.x == 0) {
             a.pair[n] = result;

@@ -23,6 +23,7 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
     int32_t *hist = reinterpret_cast<int32_t *>(smem + sizeof(uint32_t) * (size_t)a.bm_words);
     __shared__ int32_t red[2 * kScoreWarps];
     __shared__ int32_t s_node, s_xchg[2], s_bcast[2];
+    __shared__ unsigned long long red64[kScoreWarps], s_xkey, s_bkey;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int32_t id0 = rank * slice;
@@ -67,8 +68,8 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
         cl.sync();                                   // histogram complete, row(n) staged
         // ---- extraction by decreasing hist value, reduced over the cluster ----
         // As in k_score: ineligible neighbours are cleared from the slice once;
-        // each round checks the tie group of value hmax and finds the next lower
-        // value in the same scan, and one exchange over the cluster settles both.
+        // each round checks one band of values and finds the next lower value in
+        // the same scan, and one exchange over the cluster settles both.
         int32_t hloc = 0;
         for (int32_t i = threadIdx.x; i < len; i += kScoreThreads) {
             const int32_t h = hist[i];
@@ -90,35 +91,46 @@ k_score_cluster(ScoreArgs a, int32_t slice) {
         int32_t result = -1, rscore = 0;
         const int32_t per_warp = (((len + kScoreWarps - 1) / kScoreWarps) + 31) & ~31;
         const int32_t lo = warp_id() * per_warp, hi = min(len, lo + per_warp);
-        while (hmax > 0) {
-            int32_t best_id = -1, nxt = 0;
-            for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo && best_id < 0; base -= 32) {
+        // bands of values [bot, top] as in k_score: the largest valid (hist, id)
+        // in the band wins, the band doubles after a round without one
+        int32_t top = hmax, width = 1;
+        while (top > 0) {
+            const int32_t bot = max(1, top - width + 1);
+            unsigned long long best = 0ull;
+            int32_t nxt = 0;
+            for (int32_t base = lo + ((hi - lo - 1) & ~31); base >= lo; base -= 32) {
                 const int32_t i = base + lane_id();
                 const int32_t h = i < hi ? hist[i] : 0;
-                if (h < hmax) nxt = max(nxt, h);
-                unsigned ball = __ballot_sync(0xffffffffu, h == hmax);
-                while (ball && best_id < 0) {
-                    int src = 31 - __clz(ball);
+                if (h < bot) nxt = max(nxt, h);
+                const unsigned long long key = cand_key(h, id0 + i);
+                unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
+                while (ball) {
+                    const int src = 31 - __clz(ball);
                     ball &= ~(1u << src);
-                    if (warp_check(a, n, id0 + base + src, row_n, in_n, bytes)) best_id = id0 + base + src;
+                    const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
+                    if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
+                        best = ck;
                 }
+                if ((int32_t)(best >> 32) == top) break;   // nothing in the band beats it
             }
-            block_max2_i32(best_id, nxt, red);
-            if (threadIdx.x == 0) { s_xchg[0] = best_id; s_xchg[1] = nxt; }
+            block_max_key(best, nxt, red64, red);
+            if (threadIdx.x == 0) { s_xkey = best; s_xchg[1] = nxt; }
             cl.sync();
             if (threadIdx.x == 0) {
-                int32_t b = -1, x = 0;
+                unsigned long long b = 0ull;
+                int32_t x = 0;
                 for (int r = 0; r < kClusterCtas; ++r) {
-                    const int32_t *o = cl.map_shared_rank(s_xchg, r);
-                    b = max(b, o[0]);
-                    x = max(x, o[1]);
+                    const unsigned long long k = *cl.map_shared_rank(&s_xkey, r);
+                    b = k > b ? k : b;
+                    x = max(x, cl.map_shared_rank(s_xchg, r)[1]);
                 }
-                s_bcast[0] = b;
+                s_bkey = b;
                 s_bcast[1] = x;
             }
             cl.sync();
-            if (s_bcast[0] >= 0) { result = s_bcast[0]; rscore = hmax; break; }
-            hmax = s_bcast[1];
+            if (s_bkey) { result = (int32_t)(s_bkey & 0xffffffffu); rscore = (int32_t)(s_bkey >> 32); break; }
+            top = s_bcast[1];
+            width <<= 1;
         }
         if (rank == 0 && threadIdx.x == 0) {
             a.pair[n] = result;
