@@ -31,7 +31,6 @@
 namespace hgp {
 
 constexpr int kPropThreads = 1024;
-constexpr int kPropWarps = kPropThreads / 32;
 constexpr int kPartsDenseMax = 12288;   // pres + touched list: 96 KB of smem
 
 static int grid1d(int64_t n) {
@@ -342,35 +341,39 @@ __global__ void k_prop_worklist(PropArgs a) {
     }
 }
 
-template <bool DENSE>
-__global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
+template <bool DENSE, int NT>
+__global__ void __launch_bounds__(NT) k_propose(PropArgs a) {
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) int32_t smem_p[];
-    __shared__ unsigned long long red64[kPropWarps];
-    __shared__ long long red_s[kPropWarps], red_w[kPropWarps];
+    __shared__ unsigned long long red64[NW];
+    __shared__ long long red_s[NW], red_w[NW];
     __shared__ int32_t s_nt;
     // pres(n, p) per part, and the list of parts touched for this node
     int32_t *pres = DENSE ? smem_p : a.gpres + (int64_t)blockIdx.x * 2 * a.K;
     int32_t *touched = pres + a.K;
-    __shared__ int32_t s_n;
+    // the next node is fetched while the current one is worked on (double buffer)
+    __shared__ int32_t s_nb[2];
     unsigned long long nbytes = 0;
-    for (int32_t i = threadIdx.x; i < a.K; i += kPropThreads) pres[i] = 0;
-    if (threadIdx.x == 0) s_nt = 0;
+    for (int32_t i = threadIdx.x; i < a.K; i += NT) pres[i] = 0;
     const int32_t work = *a.count;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int32_t t = atomicAdd(a.next, 1);
-            s_n = t < work ? a.list[t] : a.V;
-        }
-        __syncthreads();
-        const int32_t n = s_n;
+    if (threadIdx.x == 0) {
+        s_nt = 0;
+        const int32_t t = atomicAdd(a.next, 1);
+        s_nb[0] = t < work ? a.list[t] : a.V;
+    }
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const int32_t n = s_nb[cur];
         if (n >= a.V) break;
+        int32_t t_next = 0;
+        if (threadIdx.x == 0) t_next = atomicAdd(a.next, 1);
         int32_t ps = a.rho[n];
         int32_t i0 = a.ioff[n], i1 = a.ioff[n + 1];
         long long sav = 0, wI = 0;
         // each lane fetches one hyperedge's (omega, run range); the warp walks them
-        int32_t mine = (i1 - i0 - warp_id() + kPropWarps - 1) / kPropWarps;
+        int32_t mine = (i1 - i0 - warp_id() + NW - 1) / NW;
         for (int32_t c0 = 0; c0 < mine; c0 += 32) {
-            int32_t k = i0 + warp_id() + kPropWarps * (c0 + lane_id());
+            int32_t k = i0 + warp_id() + NW * (c0 + lane_id());
             int32_t we = 0, r0 = 0, r1 = 0;
             if (c0 + lane_id() < mine) {
                 int32_t e = a.inc[k];
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         int32_t nt = s_nt;
         int32_t wn = a.w[n];
         unsigned long long best = 0;
-        for (int32_t t = threadIdx.x; t < nt; t += kPropThreads) {
+        for (int32_t t = threadIdx.x; t < nt; t += NT) {
             int32_t p = touched[t];
             if ((int64_t)a.size[p] + wn <= a.omega) {
                 unsigned long long key = ((unsigned long long)(uint32_t)pres[p] << 32) |
@@ -418,11 +421,11 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
         }
         if (lane_id() == 0) red64[warp_id()] = best;
         __syncthreads();
-        for (int32_t t = threadIdx.x; t < nt; t += kPropThreads) pres[touched[t]] = 0;
+        for (int32_t t = threadIdx.x; t < nt; t += NT) pres[touched[t]] = 0;
         if (threadIdx.x == 0) {
             unsigned long long b = 0;
             long long S = 0, W = 0;
-            for (int q = 0; q < kPropWarps; ++q) {
+            for (int q = 0; q < NW; ++q) {
                 b = red64[q] > b ? red64[q] : b;
                 S += red_s[q];
                 W += red_w[q];
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propose(PropArgs a) {
             a.gain[n] = g;
             a.pd[n] = pd;
             s_nt = 0;
+            s_nb[cur ^ 1] = t_next < work ? a.list[t_next] : a.V;
             nbytes += 8ull + 12ull;   // gain/pd writes; rho, w, I(n) offsets
         }
         __syncthreads();
@@ -517,172 +521,107 @@ __global__ void k_seq_events(int32_t M, const int32_t *mv_n, const int32_t *mv_p
 }
 
 // Edge-centric in-sequence gains (hyperedges of at most kSeqEdgeMax pins): a
-// warp per hyperedge gathers its moving pins (move index, ps, pd, whether the
-// pin is a destination); for every mover it adds up how the movers ordered
-// before it changed pins(ps, e), pins(pd, e) and their destination-only
-// variants, and writes the move's Eq. (1) change on e and its inbound-set
-// changes into the slot of (move, e): slots of move k are I(n_k) in order.
+// warp per hyperedge gathers its moving pins and sorts them by move index;
+// for every mover it adds up how the movers before it changed pins(ps, e),
+// pins(pd, e) and their destination-only variants, and adds the move's
+// Eq. (1) change on e and its inbound-set changes to the move's totals.
 constexpr int kSeqEdgeMax = 256;
 constexpr int kSeqWarps = 8;
 
-__global__ void k_move_deg1(int32_t Mcap, const int32_t *dM, const int32_t *mv_n, const int32_t *ioff,
-                            int32_t *deg) {
-    const int32_t M = *dM;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Mcap;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t n = k < M ? mv_n[k] : -1;
-        deg[k] = n >= 0 ? ioff[n + 1] - ioff[n] : 0;
-    }
-}
-
-// Same computation with each mover packed into one 64-bit word (move index,
-// ps, pd: 21 bits each; the destination bit) when every id fits 21 bits:
-// the quadratic scan then reads one broadcast shared-memory word per earlier
-// mover and updates the counts without branching.
-constexpr int kSeqPackBits = 21;
-constexpr unsigned long long kSeqPackMask = (1ull << kSeqPackBits) - 1ull;
-
 __global__ void __launch_bounds__(kSeqWarps * 32)
-k_seq_edge_packed(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *idx_of,
-                  const int32_t *mv_ps, const int32_t *mv_pd, const int32_t *src,
-                  const uint8_t *sdst, const int32_t *ioff, const int32_t *inc,
-                  const int32_t *slot0, const int32_t *nrun, const int32_t *rpart,
-                  const int32_t *rcnt, const int32_t *rcin, const int32_t *ew, int32_t *c_gain,
-                  uint8_t *c_in) {
-    __shared__ unsigned long long spk[kSeqWarps][kSeqEdgeMax];
-    __shared__ int32_t sn[kSeqWarps][kSeqEdgeMax];
+k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *idx_of,
+           const int32_t *mv_ps, const int32_t *mv_pd, const int32_t *src, const uint8_t *sdst,
+           const int32_t *nrun, const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
+           const int32_t *ew, int32_t *gseq, int32_t *lose_in, int32_t *gain_in) {
+    // per warp: the movers of one hyperedge, first as sort keys (move index,
+    // node) in the lower half, then expanded in move order to {ps, pd, weight,
+    // move index}; the weight 1 + 2^16 * [destination] adds a mover to both
+    // the plain and the destination-only count, kept in the low and high half
+    // of one register (both are pin counts of e, so at most kSeqEdgeMax).
+    // srp: the part ids of the hyperedge's runs, searched for the pre-move counts.
+    __shared__ int4 smv[kSeqWarps][kSeqEdgeMax];
+    __shared__ int32_t srp[kSeqWarps][kSeqEdgeMax];
     const int w = warp_id();
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(smv[w]);
     const unsigned lt = (1u << lane_id()) - 1u;
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t e = gw; e < E; e += nw) {
         const int32_t p0 = poff[e], p1 = poff[e + 1];
-        const int32_t se = src[e];
-        const uint8_t role = sdst[e];
         int32_t cnt = 0;
         for (int32_t base = p0; base < p1; base += 32) {
             const int32_t j = base + lane_id();
             const int32_t m = j < p1 ? pins[j] : -1;
             const int32_t k = m >= 0 ? idx_of[m] : -1;
             const unsigned ball = __ballot_sync(0xffffffffu, k >= 0);
-            if (k >= 0) {
-                const int32_t q = cnt + __popc(ball & lt);
-                spk[w][q] = ((unsigned long long)k << (2 * kSeqPackBits + 1)) |
-                            ((unsigned long long)mv_ps[k] << (kSeqPackBits + 1)) |
-                            ((unsigned long long)mv_pd[k] << 1) |
-                            (counts_in(m, se, role) ? 1ull : 0ull);
-                sn[w][q] = m;
-            }
+            if (k >= 0) skey[cnt + __popc(ball & lt)] = ((unsigned long long)k << 32) | (uint32_t)m;
             cnt += __popc(ball);
         }
+        if (cnt == 0) continue;                      // warp-uniform
+        const int32_t nr = nrun[e];
+        for (int32_t i = lane_id(); i < nr; i += 32) srp[w][i] = rpart[p0 + i];
+        // bitonic sort of the keys, padded to a power of two: move order
+        int32_t P = 1;
+        while (P < cnt) P <<= 1;
+        for (int32_t i = cnt + lane_id(); i < P; i += 32) skey[i] = ~0ull;
         __syncwarp();
-        const int32_t r0 = poff[e], r1 = r0 + nrun[e];
-        const int32_t we = ew[e];
-        for (int32_t i = lane_id(); i < cnt; i += 32) {
-            const unsigned long long ui = spk[w][i];
-            const int32_t ki = (int32_t)(ui >> (2 * kSeqPackBits + 1));
-            const int32_t psi = (int32_t)((ui >> (kSeqPackBits + 1)) & kSeqPackMask);
-            const int32_t pdi = (int32_t)((ui >> 1) & kSeqPackMask);
-            int32_t cs, csi, cd, cdi;
-            run_lookup(rpart, rcnt, rcin, r0, r1, psi, cs, csi);
-            run_lookup(rpart, rcnt, rcin, r0, r1, pdi, cd, cdi);
-            for (int32_t t = 0; t < cnt; ++t) {
-                const unsigned long long u = spk[w][t];
-                const int32_t before = (int32_t)(u >> (2 * kSeqPackBits + 1)) < ki ? 1 : 0;
-                const int32_t ps = (int32_t)((u >> (kSeqPackBits + 1)) & kSeqPackMask);
-                const int32_t pd = (int32_t)((u >> 1) & kSeqPackMask);
-                const int32_t ds = before * ((pd == psi) - (ps == psi));
-                const int32_t dd = before * ((pd == pdi) - (ps == pdi));
-                const int32_t dt = (int32_t)(u & 1ull);
-                cs += ds;
-                cd += dd;
-                csi += dt * ds;
-                cdi += dt * dd;
+        for (int32_t k2 = 2; k2 <= P; k2 <<= 1)
+            for (int32_t j = k2 >> 1; j > 0; j >>= 1) {
+                for (int32_t t = lane_id(); t < (P >> 1); t += 32) {
+                    const int32_t a = ((t & ~(j - 1)) << 1) | (t & (j - 1)), b = a + j;
+                    const unsigned long long x = skey[a], y = skey[b];
+                    if ((x > y) == ((a & k2) == 0)) { skey[a] = y; skey[b] = x; }
+                }
+                __syncwarp();
             }
-            const int32_t n = sn[w][i];
-            const int32_t pos = lower_bound_i32(inc, ioff[n], ioff[n + 1], (int32_t)e) - ioff[n];
-            const int32_t sl = slot0[ki] + pos;
-            const bool dst = (ui & 1ull) != 0;
-            c_gain[sl] = we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
-            c_in[sl] = (uint8_t)(((dst && csi == 1) ? 1 : 0) | ((dst && cdi == 0) ? 2 : 0));
-        }
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(kSeqWarps * 32)
-k_seq_edge(int32_t E, const int32_t *poff, const int32_t *pins, const int32_t *idx_of,
-           const int32_t *mv_n, const int32_t *mv_ps, const int32_t *mv_pd, const int32_t *src,
-           const uint8_t *sdst, const int32_t *ioff, const int32_t *inc, const int32_t *slot0,
-           const int32_t *nrun, const int32_t *rpart, const int32_t *rcnt, const int32_t *rcin,
-           const int32_t *ew, int32_t *c_gain, uint8_t *c_in) {
-    __shared__ int32_t sk[kSeqWarps][kSeqEdgeMax], sps[kSeqWarps][kSeqEdgeMax];
-    __shared__ int32_t spd[kSeqWarps][kSeqEdgeMax], sn[kSeqWarps][kSeqEdgeMax];
-    __shared__ uint8_t sdt[kSeqWarps][kSeqEdgeMax];
-    const int w = warp_id();
-    const unsigned lt = (1u << lane_id()) - 1u;
-    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t e = gw; e < E; e += nw) {
-        int32_t p0 = poff[e], p1 = poff[e + 1];
-        int32_t se = src[e];
+        // expand in place through registers (an entry outgrows its key)
+        const int32_t se = src[e];
         const uint8_t role = sdst[e];
-        int32_t cnt = 0;
-        for (int32_t base = p0; base < p1; base += 32) {
-            int32_t j = base + lane_id();
-            int32_t m = j < p1 ? pins[j] : -1;
-            int32_t k = m >= 0 ? idx_of[m] : -1;
-            unsigned ball = __ballot_sync(0xffffffffu, k >= 0);
-            if (k >= 0) {
-                int32_t q = cnt + __popc(ball & lt);
-                sk[w][q] = k; sps[w][q] = mv_ps[k]; spd[w][q] = mv_pd[k]; sn[w][q] = m;
-                sdt[w][q] = counts_in(m, se, role) ? 1 : 0;
-            }
-            cnt += __popc(ball);
+        unsigned long long mine[kSeqEdgeMax / 32];
+#pragma unroll
+        for (int c = 0; c < kSeqEdgeMax / 32; ++c) {
+            const int32_t i = c * 32 + lane_id();
+            mine[c] = i < cnt ? skey[i] : 0ull;
         }
         __syncwarp();
-        int32_t r0 = poff[e], r1 = r0 + nrun[e];
-        int32_t we = ew[e];
-        for (int32_t i = lane_id(); i < cnt; i += 32) {
-            int32_t ki = sk[w][i], psi = sps[w][i], pdi = spd[w][i];
-            int32_t cs, csi, cd, cdi;
-            run_lookup(rpart, rcnt, rcin, r0, r1, psi, cs, csi);
-            run_lookup(rpart, rcnt, rcin, r0, r1, pdi, cd, cdi);
-            for (int32_t t = 0; t < cnt; ++t) {
-                if (sk[w][t] >= ki) continue;
-                int32_t ps = sps[w][t], pd = spd[w][t];
-                int32_t ds = (pd == psi) - (ps == psi), dd = (pd == pdi) - (ps == pdi);
-                cs += ds; cd += dd;
-                if (sdt[w][t]) { csi += ds; cdi += dd; }
+#pragma unroll
+        for (int c = 0; c < kSeqEdgeMax / 32; ++c) {
+            const int32_t i = c * 32 + lane_id();
+            if (i < cnt) {
+                const int32_t k = (int32_t)(mine[c] >> 32), m = (int32_t)(uint32_t)mine[c];
+                smv[w][i] = make_int4(mv_ps[k], mv_pd[k], counts_in(m, se, role) ? 0x10001 : 1, k);
             }
-            int32_t n = sn[w][i];
-            int32_t pos = lower_bound_i32(inc, ioff[n], ioff[n + 1], (int32_t)e) - ioff[n];
-            int32_t s = slot0[ki] + pos;
-            bool dst = sdt[w][i] != 0;
-            c_gain[s] = we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
-            c_in[s] = (uint8_t)(((dst && csi == 1) ? 1 : 0) | ((dst && cdi == 0) ? 2 : 0));
         }
         __syncwarp();
-    }
-}
-
-// per move: gain = sum of its slots; lose / gain_in = counts of the slot bits
-__global__ void k_move_reduce1(int32_t Mcap, const int32_t *slot0, const int32_t *c_gain,
-                               const uint8_t *c_in, int32_t *gseq, int32_t *lose_in,
-                               int32_t *gain_in) {
-    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = gw; k < Mcap; k += nw) {     // moves past M have no slots: zeros
-        int32_t g = 0, lo = 0, gi = 0;
-        for (int32_t j = slot0[k] + lane_id(); j < slot0[k + 1]; j += 32) {
-            g += c_gain[j];
-            lo += c_in[j] & 1;
-            gi += c_in[j] >> 1;
+        // mover i sees the movers before it in move order; chunks of 32 are
+        // dealt out in alternating directions so every lane scans about as
+        // many predecessors as the others
+        const int32_t we = ew[e];
+        for (int32_t c = 0; c * 32 < cnt; ++c) {
+            const int32_t i = c * 32 + ((c & 1) ? 31 - lane_id() : lane_id());
+            if (i >= cnt) continue;
+            const int4 me = smv[w][i];
+            // pre-move counts: ps is always a run of e (the mover is a pin of e)
+            const int32_t qs = lower_bound_i32(srp[w], 0, nr, me.x);
+            const int32_t qd = lower_bound_i32(srp[w], 0, nr, me.y);
+            int32_t as = rcnt[p0 + qs] | (rcin[p0 + qs] << 16), ad = 0;
+            if (qd < nr && srp[w][qd] == me.y) ad = rcnt[p0 + qd] | (rcin[p0 + qd] << 16);
+            for (int32_t t = 0; t < i; ++t) {
+                const int4 v = smv[w][t];
+                if (v.y == me.x) as += v.z;
+                if (v.x == me.x) as -= v.z;
+                if (v.y == me.y) ad += v.z;
+                if (v.x == me.y) ad -= v.z;
+            }
+            const int32_t cs = as & 0xffff, csi = as >> 16, cd = ad & 0xffff, cdi = ad >> 16;
+            const bool dst = me.z != 1;
+            // integer sums: the order of the atomic adds does not matter
+            const int32_t g = we * ((cs == 1 ? 1 : 0) - (cd == 0 ? 1 : 0));
+            if (g) atomicAdd(gseq + me.w, g);
+            if (dst && csi == 1) atomicAdd(lose_in + me.w, 1);
+            if (dst && cdi == 0) atomicAdd(gain_in + me.w, 1);
         }
-        g = warp_sum(g);
-        lo = warp_sum(lo);
-        gi = warp_sum(gi);
-        if (lane_id() == 0) { gseq[k] = g; lose_in[k] = lo; gain_in[k] = gi; }
+        __syncwarp();
     }
 }
 
@@ -969,21 +908,22 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     int sms = num_sms();
     if (K <= kPartsDenseMax && !(debug & HGP_DEBUG_FORCE_GLOBAL)) {
         size_t smem = 2 * sizeof(int32_t) * (size_t)K;
-        e = allow_dynamic_smem(k_propose<true>);
+        e = allow_dynamic_smem(k_propose<true, kPropThreads>);
         if (e) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true>, kPropThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propose<true, kPropThreads>,
+                                                          kPropThreads, smem);
         if (e) return e;
         if (per_sm < 1) per_sm = 1;
         int blocks = sms * per_sm;
         if (blocks > V) blocks = V;
-        k_propose<true><<<blocks, kPropThreads, smem, s>>>(pa);
+        k_propose<true, kPropThreads><<<blocks, kPropThreads, smem, s>>>(pa);
     } else {
         int blocks = sms * 4;
         if (blocks > V) blocks = V;
         e = dalloc(tmp, &pa.gpres, (size_t)blocks * 2 * K);
         if (e) return e;
-        k_propose<false><<<blocks, kPropThreads, 0, s>>>(pa);
+        k_propose<false, kPropThreads><<<blocks, kPropThreads, 0, s>>>(pa);
     }
     count_launch();
     if (pt) {
@@ -1023,10 +963,10 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     if (!e) e = dalloc(tmp, &mv_ps, M);
     if (!e) e = dalloc(tmp, &mv_pd, M);
     if (!e) e = dalloc(tmp, &idx_of, V);
-    if (!e) e = dalloc(tmp, &gseq, M);
-    if (!e) e = dalloc(tmp, &lose, M);
-    if (!e) e = dalloc(tmp, &gin, M);
+    if (!e) e = dalloc(tmp, &gseq, 3 * (size_t)M);     // gseq, lose, gin: one block
     if (e) return e;
+    lose = gseq + M;
+    gin = gseq + 2 * (size_t)M;
     const int mbits = bits_for(wsum);
     if (edge_path) {            // unused slots: maximal key, sorted after every move
         fill_i32(reinterpret_cast<int32_t *>(mkey), (int32_t)((1u << mbits) - 1u), M, s);
@@ -1042,33 +982,14 @@ cudaError_t run_refine_pass(Arena &tmp, const Level &L, const int32_t *ew, int64
     // in-sequence gains: edge-centric when every hyperedge is small, otherwise
     // from per-(edge, part) events
     if (L.max_edge <= kSeqEdgeMax) {
-        int32_t *deg, *slot0, *c_gain;
-        uint8_t *c_in;
-        e = dalloc(tmp, &deg, M);
-        if (!e) e = dalloc(tmp, &slot0, (size_t)M + 1);
-        if (e) return e;
-        k_move_deg1<<<grid1d(M), 256, 0, s>>>(M, dM, mv_n, L.ioff, deg);
-        count_launch();
-        e = counts_to_offsets(tmp, deg, slot0, M, s);
-        if (e) return e;
-        // slots total <= P: size the buffers without a host round trip
-        e = dalloc(tmp, &c_gain, L.P);
-        if (!e) e = dalloc(tmp, &c_in, L.P);
+        e = cudaMemsetAsync(gseq, 0, sizeof(int32_t) * 3 * (size_t)M, s);   // gseq, lose, gin
         if (e) return e;
         int blocks = div_up((int64_t)L.E * 32, kSeqWarps * 32);
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         if (blocks < 1) blocks = 1;
-        if ((int64_t)V < (1ll << kSeqPackBits) && (int64_t)K < (1ll << kSeqPackBits))
-            k_seq_edge_packed<<<blocks, kSeqWarps * 32, 0, s>>>(
-                L.E, L.poff, L.pins, idx_of, mv_ps, mv_pd, L.src, L.sdst, L.ioff, L.inc, slot0,
-                R.nrun, R.rpart, R.rcnt, R.rcin, ew, c_gain, c_in);
-        else
-            k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_n, mv_ps,
-                                                         mv_pd, L.src, L.sdst, L.ioff, L.inc, slot0,
-                                                         R.nrun, R.rpart, R.rcnt, R.rcin, ew, c_gain,
-                                                         c_in);
-        count_launch();
-        k_move_reduce1<<<grid_warps(M), 256, 0, s>>>(M, slot0, c_gain, c_in, gseq, lose, gin);
+        k_seq_edge<<<blocks, kSeqWarps * 32, 0, s>>>(L.E, L.poff, L.pins, idx_of, mv_ps, mv_pd,
+                                                     L.src, L.sdst, R.nrun, R.rpart, R.rcnt, R.rcin,
+                                                     ew, gseq, lose, gin);
         count_launch();
     } else
     {

@@ -219,6 +219,29 @@ static __device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, cons
     int32_t m0 = a.noff[m], m1 = a.noff[m + 1];
     int64_t in_m = m1 - m0;
     if (in_n + in_m <= a.delta) return true;
+    if (a.bm_words && in_m <= (int64_t)a.bm_words) {
+        // in(m) is shorter than a bitmap row: walk its list and probe row(n)
+        // in shared memory; |in(n) u in(m)| = |in(n)| + |in(m) \ in(n)|
+        const int64_t room = a.delta - in_n;
+        int64_t extra = 0;
+        int32_t seen = 0;
+        for (int32_t base = m0; base < m1; base += 128) {
+            int32_t miss = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t j = base + u * 32 + lane_id();
+                if (j < m1) {
+                    const int32_t e = a.inn[j];
+                    miss += ((row_n[e >> 5] >> (e & 31)) & 1u) ? 0 : 1;
+                }
+            }
+            extra += warp_sum(miss);
+            seen += min(128, m1 - base);
+            if (extra > room) break;
+        }
+        if (lane_id() == 0) bytes += 4ull * (unsigned long long)seen;
+        return extra <= room;
+    }
     if (a.bm_words) {
         const uint4 *rm = reinterpret_cast<const uint4 *>(a.bm + (int64_t)m * a.bm_words);
         const uint4 *rn = reinterpret_cast<const uint4 *>(row_n);
