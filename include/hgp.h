@@ -75,10 +75,15 @@ typedef enum {
                                       kernel's per-CTA hash tables 64 slots, so a node with more
                                       distinct neighbours exhausts its bounded probe loop and the
                                       call returns HGP_ERR_DEVICE_LIMIT */
-#define HGP_DEBUG_FORCE_WINDOW 128u /* test knob: score every level by per-node buckets -- nodes
-                                       whose neighbour ids span at most max(64, |N_l| / 4) ids get
-                                       one CTA with a histogram over that window, the others the
-                                       8-CTA cluster (the path of levels too large for one CTA) */
+#define HGP_DEBUG_FORCE_WINDOW 128u /* test knob: score every level by per-node buckets with
+                                       histogram pieces of max(64, |N_l| / 4) ids -- one CTA takes
+                                       a node's neighbour-id window piece by piece, from the top
+                                       ids down (the path of levels too large for one CTA) */
+#define HGP_DEBUG_FORCE_HASH_BUCKET 256u /* test knob: as HGP_DEBUG_FORCE_WINDOW with single
+                                       pieces, and a 1,024-slot hash table in shared memory for the
+                                       nodes with at most 640 pin visits whose window takes more
+                                       than one piece; the rest go to the 8-CTA cluster, so all
+                                       three buckets take nodes */
 #define HGP_DEBUG_REBUILD_INC 64u  /* test knob: keep no coarse level's I(n) until refinement;
                                       rebuild each from the level's pins when refinement reaches
                                       it (the path levels beyond the memory budget take) */

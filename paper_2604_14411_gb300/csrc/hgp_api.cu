@@ -313,7 +313,7 @@ static int partition_on(hgp_graph *g, int64_t omega, int64_t delta, const hgp_op
         if (opt->debug & ~(uint32_t)(HGP_DEBUG_KEEP_LEVELS | HGP_DEBUG_TIMING | HGP_DEBUG_FORCE_GLOBAL |
                                      HGP_DEBUG_NO_BITMAP | HGP_DEBUG_FORCE_CLUSTER |
                                      HGP_DEBUG_SMALL_TABLE | HGP_DEBUG_REBUILD_INC |
-                                     HGP_DEBUG_FORCE_WINDOW))
+                                     HGP_DEBUG_FORCE_WINDOW | HGP_DEBUG_FORCE_HASH_BUCKET))
             return fail(g, HGP_ERR_INVALID_ARG, "unknown debug bits");
         passes = opt->refine_passes;
         debug = opt->debug;

@@ -18,6 +18,9 @@ int64_t bitmap_budget() {
     return b < (16ll << 30) ? b : (16ll << 30);
 }
 constexpr int32_t kBitmapMaxWords = 8192;       // 32 KB row in shared memory
+// Largest number of wcap-id pieces one scoring CTA takes for a node's window
+// (each piece re-reads the node's pins; wider windows go to the 8-CTA cluster).
+constexpr int32_t kMaxWindows = 8;
 
 // ---- per-node work buckets for levels too large for one CTA's histogram ----
 // A node whose neighbour ids all lie in a window of at most wcap ids (as in
@@ -46,44 +49,62 @@ static __global__ void k_edge_span(int32_t E, const int32_t *poff, const int32_t
     }
 }
 
-// window of every node and its bucket (fit = 1: one CTA over the window;
-// nodes known to have no candidate go there too, they are answered at once)
+// window of every node and its bucket: 0 = one CTA over the window, in
+// pieces of wcap ids taken one after another (nodes known to have no
+// candidate go there too, they are answered at once); 1 = one CTA with a
+// shared hash table, when the window takes more than one piece, the node's pin
+// visits (an upper bound on its distinct neighbours) stay below hmax_visits
+// and its weight sum over I(n) (an upper bound on every hist(n, m)) below
+// wlimit; 0 again when at most max_windows pieces cover the window; 2 = the rest
 static __global__ void k_node_window(int32_t V, const int32_t *ioff, const int32_t *inc,
+                                     const int32_t *poff, const int32_t *ew,
                                      const int32_t *emin, const int32_t *emax, const uint8_t *dead,
-                                     int32_t wcap, int32_t *wlo, int32_t *whi, int32_t *fit,
-                                     int32_t *nofit) {
+                                     int32_t wcap, int32_t max_windows, int64_t hmax_visits,
+                                     int64_t wlimit,
+                                     int32_t *wlo, int32_t *whi, int32_t *b0, int32_t *b1,
+                                     int32_t *b2) {
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t n = gw; n < V; n += nw) {
         int32_t lo = 0x7fffffff, hi = -1;
+        long long visits = 0, wsum = 0;
         for (int32_t k = ioff[n] + lane_id(); k < ioff[n + 1]; k += 32) {
             const int32_t e = inc[k];
             lo = min(lo, emin[e]);
             hi = max(hi, emax[e]);
+            visits += poff[e + 1] - poff[e];
+            wsum += ew[e];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            visits += __shfl_xor_sync(0xffffffffu, visits, o);
+            wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         }
         if (lane_id() == 0) {
             if (hi < lo) { lo = 0; hi = -1; }            // no hyperedge: an empty window
             wlo[n] = lo;
             whi[n] = hi;
-            const int f = (dead && dead[n]) || (int64_t)hi - lo + 1 <= wcap;
-            fit[n] = f;
-            nofit[n] = 1 - f;
+            const int64_t span = (int64_t)hi - lo + 1;
+            const int one = (dead && dead[n]) || span <= wcap;
+            const int h = !one && visits <= hmax_visits && wsum < wlimit;
+            const int f = one || (!h && span <= (int64_t)wcap * max_windows);
+            b0[n] = f;
+            b1[n] = h;
+            b2[n] = 1 - f - h;
         }
     }
 }
 
-static __global__ void k_bucket_lists(int32_t V, const int32_t *fit, const int32_t *rank_fit,
-                                      const int32_t *rank_nofit, int32_t *list_fit,
-                                      int32_t *list_nofit) {
+static __global__ void k_bucket_lists(int32_t V, const int32_t *b0, const int32_t *b1,
+                                      const int32_t *r0, const int32_t *r1, const int32_t *r2,
+                                      int32_t *l0, int32_t *l1, int32_t *l2) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (fit[i]) list_fit[rank_fit[i]] = (int32_t)i;
-        else list_nofit[rank_nofit[i]] = (int32_t)i;
+        if (b0[i]) l0[r0[i]] = (int32_t)i;
+        else if (b1[i]) l1[r1[i]] = (int32_t)i;
+        else l2[r2[i]] = (int32_t)i;
     }
 }
 
@@ -160,28 +181,41 @@ cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const
     }
     size_t row_bytes = sizeof(uint32_t) * (size_t)a.bm_words;
     size_t dense_smem = row_bytes + sizeof(int32_t) * (size_t)L.V;
+    const uint32_t buckets = HGP_DEBUG_FORCE_WINDOW | HGP_DEBUG_FORCE_HASH_BUCKET;
     bool dense = dense_smem + 2048 <= (size_t)max_smem &&
-                 !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER | HGP_DEBUG_FORCE_WINDOW));
+                 !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER | buckets));
     int sms = num_sms();
     int64_t wcap = ((int64_t)max_smem - 2048 - (int64_t)row_bytes) / 4;
-    if (debug & HGP_DEBUG_FORCE_WINDOW) {   // test knob: small windows, so both buckets are used
+    if (debug & buckets) {                  // test knob: small windows, so every bucket is used
         int64_t small = L.V / 4 > 64 ? L.V / 4 : 64;
         if (small < wcap) wcap = small;
     }
     if (!dense && wcap >= 64 && !(debug & (HGP_DEBUG_FORCE_GLOBAL | HGP_DEBUG_FORCE_CLUSTER))) {
-        int32_t *emin, *emax, *wlo, *whi, *fit, *nofit, *rfit, *rnofit, *lfit, *lnofit, *cnt;
+        int32_t *emin, *emax, *wlo, *whi, *bk[3], *rk[3], *lst[3], *cnt;
         e = dalloc(ar, &emin, L.E);
         if (!e) e = dalloc(ar, &emax, L.E);
         if (!e) e = dalloc(ar, &wlo, L.V);
         if (!e) e = dalloc(ar, &whi, L.V);
-        if (!e) e = dalloc(ar, &fit, L.V);
-        if (!e) e = dalloc(ar, &nofit, L.V);
-        if (!e) e = dalloc(ar, &rfit, L.V);
-        if (!e) e = dalloc(ar, &rnofit, L.V);
-        if (!e) e = dalloc(ar, &lfit, L.V);
-        if (!e) e = dalloc(ar, &lnofit, L.V);
+        for (int k = 0; k < 3 && !e; ++k) {
+            e = dalloc(ar, &bk[k], L.V);
+            if (!e) e = dalloc(ar, &rk[k], L.V);
+            if (!e) e = dalloc(ar, &lst[k], L.V);
+        }
         if (!e) e = dalloc(ar, &cnt, 3);
         if (e) return e;
+        // shared hash bucket: packed 32-bit slots after row(n); the id field
+        // holds id + 1 (0 = empty), the rest of the word the count
+        const int kbits = 32 - __builtin_clz((unsigned)L.V);
+        const int vbits = 32 - kbits;
+        int64_t scap = ((int64_t)max_smem - 2048 - (int64_t)row_bytes) / 4;
+        scap &= ~(int64_t)31;
+        int64_t hvisits = scap * 5 / 8;                   // load factor at most 5/8
+        int64_t wlimit = vbits >= 4 ? (1ll << vbits) : 0;
+        if (debug & HGP_DEBUG_FORCE_HASH_BUCKET) {      // test knob: a small table
+            scap = scap < 1024 ? scap : 1024;
+            hvisits = scap * 5 / 8;
+        }
+        if (scap < 1024 || wlimit == 0 || (debug & HGP_DEBUG_FORCE_WINDOW)) hvisits = -1;
         int wb = div_up((int64_t)(L.E > L.V ? L.E : L.V) * 32, 256);
         if (wb > sms * 16) wb = sms * 16;
         if (wb < 1) wb = 1;
@@ -189,21 +223,25 @@ cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const
             k_edge_span<<<wb, 256, 0, s>>>(L.E, L.poff, L.pins, emin, emax);
             count_launch();
         }
-        k_node_window<<<wb, 256, 0, s>>>(L.V, L.ioff, L.inc, emin, emax, L.dead, (int32_t)wcap, wlo,
-                                         whi, fit, nofit);
+        // windows per node: up to kMaxWindows pieces of wcap ids (single pieces
+        // under the hash-bucket test knob, so that the cluster takes the rest)
+        const int32_t maxw = (debug & HGP_DEBUG_FORCE_HASH_BUCKET) ? 1 : kMaxWindows;
+        k_node_window<<<wb, 256, 0, s>>>(L.V, L.ioff, L.inc, L.poff, ew, emin, emax, L.dead,
+                                         (int32_t)wcap, maxw, hvisits, wlimit, wlo, whi, bk[0],
+                                         bk[1], bk[2]);
         count_launch();
-        e = exclusive_scan_i32(ar, fit, rfit, L.V, cnt, s);
-        if (!e) e = exclusive_scan_i32(ar, nofit, rnofit, L.V, cnt + 1, s);
+        for (int k = 0; k < 3 && !e; ++k) e = exclusive_scan_i32(ar, bk[k], rk[k], L.V, cnt + k, s);
         if (e) return e;
         k_bucket_lists<<<div_up(L.V, 256) < sms * 8 ? div_up(L.V, 256) : sms * 8, 256, 0, s>>>(
-            L.V, fit, rfit, rnofit, lfit, lnofit);
+            L.V, bk[0], bk[1], rk[0], rk[1], rk[2], lst[0], lst[1], lst[2]);
         count_launch();
-        // bucket 1: one CTA per node over its window
+        // bucket 0: one CTA per node over its window, piece by piece
         ScoreArgs w = a;
-        w.nodes = lfit;
+        w.nodes = lst[0];
         w.count = cnt;
         w.wlo = wlo;
         w.whi = whi;
+        w.wcap = (int32_t)wcap;
         size_t wsmem = row_bytes + sizeof(int32_t) * (size_t)wcap;
         e = allow_dynamic_smem(k_score<true>);
         if (e) return e;
@@ -217,9 +255,30 @@ cudaError_t run_score(Arena &ar, Arena &roll, Level &L, const Level *prev, const
         count_launch();
         e = cudaGetLastError();
         if (e) return e;
+        // bucket 1: one CTA per node with a shared hash table
+        if (hvisits > 0) {
+            ScoreArgs h = a;
+            h.nodes = lst[1];
+            h.count = cnt + 1;
+            h.scap = (int32_t)scap;
+            h.vbits = vbits;
+            e = dalloc(ar, &h.next, 1);
+            if (!e) e = cudaMemsetAsync(h.next, 0, sizeof(int32_t), s);
+            if (e) return e;
+            size_t hsmem = row_bytes + sizeof(uint32_t) * (size_t)scap;
+            auto hk = k_score<false, kScoreThreads, true>;
+            e = allow_dynamic_smem(hk);
+            if (e) return e;
+            blocks = sms;
+            if (blocks > L.V) blocks = L.V;
+            hk<<<blocks, kScoreThreads, hsmem, s>>>(h);
+            count_launch();
+            e = cudaGetLastError();
+            if (e) return e;
+        }
         // bucket 2: the rest, on the cluster (or the hash tables below)
-        a.nodes = lnofit;
-        a.count = cnt + 1;
+        a.nodes = lst[2];
+        a.count = cnt + 2;
         e = dalloc(ar, &a.next, 1);
         if (!e) e = cudaMemsetAsync(a.next, 0, sizeof(int32_t), s);
         if (e) return e;

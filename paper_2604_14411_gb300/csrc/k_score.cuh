@@ -41,6 +41,11 @@ struct ScoreArgs {
     int32_t *status;
     int32_t *gkeys, *gvals;          // hash mode: per-CTA tables of gcap entries
     int32_t gcap;
+    int32_t wcap;                    // dense mode: table entries (0 = V, one window)
+    // shared hash mode: scap packed slots ((id + 1) << vbits | hist) in shared
+    // memory; every node scored this way has fewer pin visits than 5/8 scap and
+    // a weight sum over I(n) below 2^vbits, so neither probing nor a count can overflow
+    int32_t scap, vbits;
     unsigned long long *bytes;
     const uint32_t *bm;              // bitmap mode: [V][bm_words] rows of in()
     int32_t bm_words;                // multiple of 4 (16-byte rows); 0 = list mode
@@ -277,7 +282,7 @@ static __device__ bool warp_check(const ScoreArgs &a, int32_t n, int32_t m, cons
 // NT threads per CTA: 1024 (one CTA per SM), or 512 with two CTAs per SM when
 // two histograms fit (shorter barriers, one CTA's extraction overlapping the
 // other's gather).
-template <bool DENSE, int NT = kScoreThreads>
+template <bool DENSE, int NT = kScoreThreads, bool SHASH = false>
 __global__ void __launch_bounds__(NT, kScoreThreads / NT)
 k_score(ScoreArgs a) {
     constexpr int NW = NT / 32;
@@ -288,8 +293,10 @@ k_score(ScoreArgs a) {
     __shared__ int32_t red[2 * NW];
     __shared__ unsigned long long red64[NW];
 
-    int32_t *gkeys = DENSE ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
-    int32_t *gvals = DENSE ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
+    int32_t *gkeys = (DENSE || SHASH) ? nullptr : a.gkeys + (int64_t)blockIdx.x * a.gcap;
+    int32_t *gvals = (DENSE || SHASH) ? nullptr : a.gvals + (int64_t)blockIdx.x * a.gcap;
+    uint32_t *stab = reinterpret_cast<uint32_t *>(hist);       // shared hash slots
+    const uint32_t vmask = SHASH ? ((1u << a.vbits) - 1u) : 0u;
     const uint32_t mask = (uint32_t)a.gcap - 1u;
     unsigned long long bytes = 0;
 
@@ -307,118 +314,164 @@ k_score(ScoreArgs a) {
             continue;
         }
         const unsigned long long thr = a.thr ? a.thr[n] : 0ull;
-        // dense table: ids base .. base + cap - 1 (the node's window, or all)
-        const int32_t base = (DENSE && a.wlo) ? a.wlo[n] : 0;
-        const int32_t cap = DENSE ? (a.wlo ? max(0, a.whi[n] - base + 1) : a.V) : a.gcap;
-        // ---- clear; stage row(n) ----
-        for (int32_t i = threadIdx.x; i < cap; i += NT) {
-            if (DENSE) hist[i] = 0;
-            else { gkeys[i] = -1; gvals[i] = 0; }
-        }
         if (a.bm_words) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.bm + (int64_t)n * a.bm_words);
             uint4 *dst = reinterpret_cast<uint4 *>(row_n);
             for (int32_t i = threadIdx.x; i < (a.bm_words >> 2); i += NT) dst[i] = src[i];
         }
-        __syncthreads();
-        // ---- Eq. (2) accumulation: warp w takes hyperedges i0 + w, i0 + w + W, ... ----
-        {
-            const int32_t i0 = a.ioff[n], deg = a.ioff[n + 1] - i0;
-            const int32_t mine = (deg - warp_id() + NW - 1) / NW;
-            if (DENSE) {
-                warp_accumulate(a, n, i0, warp_id(), NW, mine,
-                                [&](int32_t m, int32_t wt) { atomicAdd(&hist[m - base], wt); }, bytes);
-            } else {
-                warp_accumulate(a, n, i0, warp_id(), NW, mine,
-                                [&](int32_t m, int32_t wt) {
-                                    uint32_t slot = hash_u32((uint32_t)m) & mask;
-                                    for (int32_t probes = 0;;) {
-                                        int32_t kk = atomicCAS(&gkeys[slot], -1, m);
-                                        if (kk == -1 || kk == m) { atomicAdd(&gvals[slot], wt); break; }
-                                        slot = (slot + 1) & mask;
-                                        if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
-                                    }
-                                }, bytes);
-            }
-        }
-        __syncthreads();
-        // ---- extraction by decreasing hist value ----
-        // Which neighbours may be the candidate does not change during the
-        // extraction (eligible() depends on m and hist(n, m) only), so the
-        // others are cleared from the table once; every round then scans the
-        // table in shared memory alone, checking the tie group of value hmax
-        // and finding the next lower value in the same pass.
-        int32_t hmax = 0;
-        for (int32_t i = threadIdx.x; i < cap; i += NT) {
-            const int32_t h = DENSE ? hist[i] : (gkeys[i] >= 0 ? gvals[i] : 0);
-            if (h <= 0) continue;
-            if (!eligible(a, DENSE ? base + i : gkeys[i], h, thr)) {
-                if (DENSE) hist[i] = 0; else gvals[i] = 0;
-            } else {
-                hmax = max(hmax, h);
-            }
-        }
-        hmax = block_max_i32<NW>(hmax, red);
         const int64_t in_n = a.noff[n + 1] - a.noff[n];
-        int32_t result = -1, rscore = 0;
-        const int32_t per_warp = (((cap + NW - 1) / NW) + 31) & ~31;
-        const int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
-        // Rounds over bands of values [bot, top]: every candidate in the band
-        // is checked and the largest valid (hist, id) wins -- the first valid
-        // one in the (hist desc, id desc) order, since every value above the
-        // band has been checked already.  The first band is the top value
-        // alone; after each round without a valid candidate the band doubles
-        // (a node facing saturated clusters fails many groups in a row).  nxt
-        // = the largest value below the band, complete whenever no warp ended
-        // its scan early (only a find at the band's top ends it).
-        int32_t top = hmax, width = 1;
-        while (top > 0) {
-            const int32_t bot = max(1, top - width + 1);
-            unsigned long long best = 0ull;           // this warp's best valid key
-            int32_t nxt = 0;
-            if (DENSE) {
-                // ids are table indices: scan downwards, so within one value the
-                // first valid candidate is the warp's best
-                for (int32_t b0 = lo + ((hi - lo - 1) & ~31); b0 >= lo; b0 -= 32) {
-                    const int32_t i = b0 + lane_id();
-                    const int32_t h = i < hi ? hist[i] : 0;
-                    if (h < bot) nxt = max(nxt, h);
-                    const unsigned long long key = cand_key(h, base + i);
-                    unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
-                    while (ball) {
-                        const int src = 31 - __clz(ball);
-                        ball &= ~(1u << src);
-                        const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
-                        if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
-                            best = ck;
-                    }
-                    if ((int32_t)(best >> 32) == top) break;   // nothing in the band beats it
-                }
-            } else {
-                for (int32_t b0 = lo; b0 < hi; b0 += 32) {
-                    const int32_t i = b0 + lane_id();
-                    int32_t h = 0;
-                    unsigned long long key = 0ull;
-                    if (i < hi && gkeys[i] >= 0) {
-                        h = gvals[i];
-                        key = cand_key(h, gkeys[i]);
-                        if (h < bot) nxt = max(nxt, h);
-                    }
-                    unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
-                    while (ball) {
-                        const int src = __ffs(ball) - 1;
-                        ball &= ball - 1;
-                        const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
-                        if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
-                            best = ck;
-                    }
+        // Dense table: the node's neighbour ids lo_n .. hi_n (its window, or
+        // all ids) in windows of at most wcap ids, taken from the top down;
+        // the hash modes have one table.  The answer is the largest valid
+        // (hist, id) over all windows.
+        const int32_t lo_n = (DENSE && a.wlo) ? a.wlo[n] : 0;
+        const int32_t hi_n = DENSE ? (a.wlo ? a.whi[n] : a.V - 1) : 0;
+        const int32_t wcap = a.wcap > 0 ? a.wcap : a.V;
+        unsigned long long best_all = 0ull;
+        for (int32_t wtop = hi_n;; wtop -= wcap) {
+            const int32_t base = DENSE ? max(lo_n, wtop - wcap + 1) : 0;
+            const int32_t cap = DENSE ? max(0, wtop - base + 1) : (SHASH ? a.scap : a.gcap);
+            // ---- clear ----
+            for (int32_t i = threadIdx.x; i < cap; i += NT) {
+                if (DENSE) hist[i] = 0;
+                else if (SHASH) stab[i] = 0u;
+                else { gkeys[i] = -1; gvals[i] = 0; }
+            }
+            __syncthreads();
+            // ---- Eq. (2) accumulation: warp w takes hyperedges i0 + w, i0 + w + W, ... ----
+            {
+                const int32_t i0 = a.ioff[n], deg = a.ioff[n + 1] - i0;
+                const int32_t mine = (deg - warp_id() + NW - 1) / NW;
+                if (DENSE) {
+                    warp_accumulate(a, n, i0, warp_id(), NW, mine,
+                                    [&](int32_t m, int32_t wt) {
+                                        if ((uint32_t)(m - base) < (uint32_t)cap) atomicAdd(&hist[m - base], wt);
+                                    }, bytes);
+                } else if (SHASH) {
+                    // linear probing from a multiplicative hash; a slot's id never
+                    // changes once set, so a plain read that sees it is conclusive
+                    warp_accumulate(a, n, i0, warp_id(), NW, mine,
+                                    [&](int32_t m, int32_t wt) {
+                                        const uint32_t tag = (uint32_t)(m + 1) << a.vbits;
+                                        uint32_t slot = (uint32_t)(((unsigned long long)hash_u32((uint32_t)m) *
+                                                                    (uint32_t)cap) >> 32);
+                                        for (int32_t probes = 0;;) {
+                                            uint32_t cur = *reinterpret_cast<volatile uint32_t *>(&stab[slot]);
+                                            if (cur == 0u) {
+                                                cur = atomicCAS(&stab[slot], 0u, tag | (uint32_t)wt);
+                                                if (cur == 0u) break;
+                                            }
+                                            if ((cur & ~vmask) == tag) { atomicAdd(&stab[slot], (uint32_t)wt); break; }
+                                            slot = slot + 1u == (uint32_t)cap ? 0u : slot + 1u;
+                                            if (++probes >= cap) { set_status(a.status, kDevLimit); break; }
+                                        }
+                                    }, bytes);
+                } else {
+                    warp_accumulate(a, n, i0, warp_id(), NW, mine,
+                                    [&](int32_t m, int32_t wt) {
+                                        uint32_t slot = hash_u32((uint32_t)m) & mask;
+                                        for (int32_t probes = 0;;) {
+                                            int32_t kk = atomicCAS(&gkeys[slot], -1, m);
+                                            if (kk == -1 || kk == m) { atomicAdd(&gvals[slot], wt); break; }
+                                            slot = (slot + 1) & mask;
+                                            if (++probes >= a.gcap) { set_status(a.status, kDevLimit); break; }
+                                        }
+                                    }, bytes);
                 }
             }
-            block_max_key<NW>(best, nxt, red64, red);
-            if (best) { result = (int32_t)(best & 0xffffffffu); rscore = (int32_t)(best >> 32); break; }
-            top = nxt;
-            width <<= 1;
+            __syncthreads();
+            // ---- extraction by decreasing hist value ----
+            // Which neighbours may be the candidate does not change during the
+            // extraction (eligible() depends on m and hist(n, m) only), so the
+            // others are cleared from the table once; every round then scans the
+            // table in shared memory alone, checking the tie group of value hmax
+            // and finding the next lower value in the same pass.
+            int32_t hmax = 0;
+            for (int32_t i = threadIdx.x; i < cap; i += NT) {
+                const int32_t h = DENSE ? hist[i]
+                                  : SHASH ? (int32_t)(stab[i] & vmask) : (gkeys[i] >= 0 ? gvals[i] : 0);
+                if (h <= 0) continue;
+                const int32_t m = DENSE ? base + i : SHASH ? (int32_t)(stab[i] >> a.vbits) - 1 : gkeys[i];
+                if (!eligible(a, m, h, thr)) {
+                    if (DENSE) hist[i] = 0;
+                    else if (SHASH) stab[i] &= ~vmask;        // the id stays, the count drops to 0
+                    else gvals[i] = 0;
+                } else {
+                    hmax = max(hmax, h);
+                }
+            }
+            hmax = block_max_i32<NW>(hmax, red);
+            const int32_t per_warp = (((cap + NW - 1) / NW) + 31) & ~31;
+            const int32_t lo = warp_id() * per_warp, hi = min(cap, lo + per_warp);
+            // Rounds over bands of values [bot, top]: every candidate in the band
+            // that beats the best so far is checked and the largest valid (hist,
+            // id) wins -- the first valid one in the (hist desc, id desc) order,
+            // since every value above the band has been checked already.  The
+            // first band is the top value alone; after each round without a valid
+            // candidate the band doubles (a node facing saturated clusters fails
+            // many groups in a row).  nxt = the largest value below the band,
+            // complete whenever no warp ended its scan early (only a find at the
+            // band's top ends it).  best_all carries the best of the windows above,
+            // whose ids are all larger: only a larger hist can beat it here.
+            int32_t top = hmax, width = 1;
+            while (top > (int32_t)(best_all >> 32)) {
+                const int32_t bot = max(1, top - width + 1);
+                unsigned long long best = best_all;       // this warp's best valid key
+                int32_t nxt = 0;
+                if (DENSE) {
+                    // ids are table indices: scan downwards, so within one value the
+                    // first valid candidate is the warp's best
+                    for (int32_t b0 = lo + ((hi - lo - 1) & ~31); b0 >= lo; b0 -= 32) {
+                        const int32_t i = b0 + lane_id();
+                        const int32_t h = i < hi ? hist[i] : 0;
+                        if (h < bot) nxt = max(nxt, h);
+                        const unsigned long long key = cand_key(h, base + i);
+                        unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
+                        while (ball) {
+                            const int src = 31 - __clz(ball);
+                            ball &= ~(1u << src);
+                            const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
+                            if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
+                                best = ck;
+                        }
+                        if ((int32_t)(best >> 32) == top) break;   // nothing in the band beats it
+                    }
+                } else {
+                    for (int32_t b0 = lo; b0 < hi; b0 += 32) {
+                        const int32_t i = b0 + lane_id();
+                        int32_t h = 0;
+                        unsigned long long key = 0ull;
+                        if (SHASH) {
+                            const uint32_t u = i < hi ? stab[i] : 0u;
+                            h = (int32_t)(u & vmask);
+                            key = cand_key(h, (int32_t)(u >> a.vbits) - 1);
+                            if (h < bot) nxt = max(nxt, h);
+                        } else if (i < hi && gkeys[i] >= 0) {
+                            h = gvals[i];
+                            key = cand_key(h, gkeys[i]);
+                            if (h < bot) nxt = max(nxt, h);
+                        }
+                        unsigned ball = __ballot_sync(0xffffffffu, h >= bot && h <= top && key > best);
+                        while (ball) {
+                            const int src = __ffs(ball) - 1;
+                            ball &= ball - 1;
+                            const unsigned long long ck = __shfl_sync(0xffffffffu, key, src);
+                            if (ck > best && warp_check(a, n, (int32_t)(ck & 0xffffffffu), row_n, in_n, bytes))
+                                best = ck;
+                        }
+                    }
+                }
+                block_max_key<NW>(best, nxt, red64, red);
+                best_all = best;
+                if ((int32_t)(best_all >> 32) >= bot) break;   // nothing below the band beats it
+                top = nxt;
+                width <<= 1;
+            }
+            if (!DENSE || base <= lo_n) break;
+            __syncthreads();      // every read of this window done before the next one's clear
         }
+        const int32_t result = best_all ? (int32_t)(best_all & 0xffffffffu) : -1;
+        const int32_t rscore = (int32_t)(best_all >> 32);
         if (threadIdx.x == 0) {
             a.pair[n] = result;
             a.score[n] = result >= 0 ? rscore : 0;

@@ -33,6 +33,7 @@ HGP_DEBUG_FORCE_CLUSTER = 16
 HGP_DEBUG_SMALL_TABLE = 32
 HGP_DEBUG_REBUILD_INC = 64
 HGP_DEBUG_FORCE_WINDOW = 128
+HGP_DEBUG_FORCE_HASH_BUCKET = 256
 (HGP_LEVEL_PAIR, HGP_LEVEL_SCORE, HGP_LEVEL_MATCH, HGP_LEVEL_GAMMA, HGP_LEVEL_RHO_IN,
  HGP_LEVEL_RHO_OUT, HGP_LEVEL_WEIGHT, HGP_LEVEL_REFINE, HGP_LEVEL_KEY,
  HGP_LEVEL_GAIN_SEQ) = range(10)

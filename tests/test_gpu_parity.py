@@ -127,7 +127,9 @@ def test_weighted():
                                    H.HGP_DEBUG_FORCE_CLUSTER,
                                    H.HGP_DEBUG_FORCE_CLUSTER | H.HGP_DEBUG_NO_BITMAP,
                                    H.HGP_DEBUG_REBUILD_INC, H.HGP_DEBUG_FORCE_WINDOW,
-                                   H.HGP_DEBUG_FORCE_WINDOW | H.HGP_DEBUG_NO_BITMAP])
+                                   H.HGP_DEBUG_FORCE_WINDOW | H.HGP_DEBUG_NO_BITMAP,
+                                   H.HGP_DEBUG_FORCE_HASH_BUCKET,
+                                   H.HGP_DEBUG_FORCE_HASH_BUCKET | H.HGP_DEBUG_NO_BITMAP])
 def test_fallback_paths(debug):
     compare(synth.random_snn(700, 12, 8), 20, 80, debug=debug)
 
@@ -137,10 +139,36 @@ def test_fallback_paths(debug):
     (lambda: synth.conv_snn(6, 8, 8, 6, 12, 5), 64, 300),
     (lambda: synth.snn_2k(0), 128, 512)])
 def test_window_buckets(make, omega, delta):
-    """Per-node buckets (the path of levels too large for one CTA): nodes
-    whose neighbour ids fit a small window get one CTA over that window, the
-    rest the 8-CTA cluster; layered graphs put many nodes in each bucket."""
+    """Per-node buckets (the path of levels too large for one CTA): one CTA
+    takes a node's neighbour-id window in pieces of a quarter of the ids,
+    from the top down, carrying the best valid candidate across pieces;
+    layered graphs need one piece for most nodes, random ones up to four."""
     compare(make(), omega, delta, debug=H.HGP_DEBUG_FORCE_WINDOW)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_window_pieces_weighted(seed):
+    """Pieces with weighted hyperedges and nodes: ties and near-ties of hist
+    across piece boundaries decide the pair by id."""
+    g = synth.random_snn(800, 10, 30 + seed, size_max=30)
+    rng = np.random.default_rng(seed)
+    g.node_weights = rng.integers(1, 4, size=g.num_nodes).astype(np.int32)
+    g.edge_weights = rng.integers(1, 4, size=g.num_edges).astype(np.int32)
+    compare(g, 30, 120, debug=H.HGP_DEBUG_FORCE_WINDOW)
+
+
+@pytest.mark.parametrize("make,omega,delta", [
+    (lambda: synth.random_snn(1200, 16, 21), 24, 160),
+    (lambda: synth.random_snn(900, 24, 4, size_max=40), 40, 300),
+    (lambda: synth.conv_snn(6, 8, 8, 6, 12, 5), 64, 300),
+    (lambda: synth.snn_2k(0), 128, 512)])
+def test_hash_bucket(make, omega, delta):
+    """The shared-memory hash bucket of large levels: nodes with few pin
+    visits are scored by one CTA whose histogram is a hash table of packed
+    (id, count) slots in shared memory, between the window bucket and the
+    8-CTA cluster; the knob cuts the table to 1,024 slots so that all three
+    buckets take nodes."""
+    compare(make(), omega, delta, debug=H.HGP_DEBUG_FORCE_HASH_BUCKET)
 
 
 @pytest.mark.parametrize("make,omega,delta,passes,incident", [
