@@ -97,8 +97,9 @@ def _recount(g, ids):
 def test_batch64_full_size():
     """The 64-instance batch of the bench (150.8 M pins) in one
     hgp_partition_batch call: the members whose oracle results
-    tests/golden/make_expected.py stored (every conv-style member and seven
-    random ones) bit-exact, every member recounted (cost, bounds)."""
+    tests/golden/make_expected.py stored (every conv-style member and the
+    random ones whose oracle runs have finished) bit-exact, every member
+    recounted (cost, bounds)."""
     import hashlib
     import os
     from conftest import ROOT

@@ -4,8 +4,9 @@ random SNN, 67M pins; 204,800-node layered conv-style SNN, ~1.4e8 pins).
 A whole partition of these takes hundreds of coarsening levels and far more
 oracle time than a test can spend, so the test runs the first matching only
 (max_levels = 1, no refinement) at full size, in the scoring kernel's
-large-level configuration (the 8-CTA distributed shared-memory histogram),
-and checks:
+large-level configuration (one CTA per node over its neighbour-id window in
+pieces; for the SNN also the 8-CTA distributed shared-memory histogram, whose
+pair and score must agree on every node), and checks:
   - candidate and score of 512 seeded sampled nodes against the oracle,
     which computes them one node at a time (Eq. 2, Sec. III-B.2);
   - the matching properties of Sec. III-A / III-B.3 on every node;
@@ -90,6 +91,12 @@ def test_first_level_full_size(name, make, omega, delta):
     assert np.array_equal(inbound[:res.num_parts], res.part_inbound)
     assert weight.max() <= omega and inbound.max() <= delta
     assert res.num_parts == g.num_nodes - int((match != np.arange(g.num_nodes)).sum()) // 2
+    if name == "snn256k":
+        with hgp.Graph.from_hypergraph(g) as G:
+            G.partition(omega, delta, refine_passes=0, max_levels=1,
+                        debug=H.HGP_DEBUG_KEEP_LEVELS | H.HGP_DEBUG_FORCE_CLUSTER)
+            assert np.array_equal(G.level_array(0, H.HGP_LEVEL_PAIR), pair)
+            assert np.array_equal(G.level_array(0, H.HGP_LEVEL_SCORE), score)
 
 
 def test_learned_order_on_the_256k_snn():
