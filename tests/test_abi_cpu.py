@@ -125,3 +125,22 @@ def test_model_from_params_rounds_to_nearest_even():
     assert got[:4].tolist() == [0x3F80, 0x3F82, 0xBF80, 0x4000]
     with pytest.raises(H.HgpError):
         H.hgp_model_from_params(p, 21)
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/hgp.h that the binding mirrors has the
+    header's value, and every flag and debug bit is mirrored."""
+    from paper_2604_14411_gb300 import hgp as H
+    src = open(os.path.join(ROOT, "include", "hgp.h")).read()
+    defs = {k: int(v, 0) for k, v in re.findall(r"#define\s+(HGP_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)u?\b", src)}
+    assert defs, "no #define constants found"
+    mirrored = 0
+    for name, value in defs.items():
+        if hasattr(H, name):
+            assert getattr(H, name) == value, name
+            mirrored += 1
+        else:
+            assert not name.startswith(("HGP_DEBUG_", "HGP_DELTA_", "HGP_ERR_")), f"{name} not in the binding"
+    assert mirrored >= 10
+    bits = [v for k, v in defs.items() if k.startswith("HGP_DEBUG_")]
+    assert all(b & (b - 1) == 0 for b in bits) and len(set(bits)) == len(bits)   # distinct single bits
